@@ -1,0 +1,343 @@
+"""Benchmark of the JFNK-MG hot path on one or more GB300s.
+
+Workload (one "step" = one complete inexact-Newton solve of the whole hot path):
+3D nonlinear diffusion -div((1+u^2) grad u) = f on the unit cube, Q1 on 129^3
+nodes (2,048,383 unknowns), f manufactured from u* = sin(pi x) sin(pi y)
+sin(pi z), u0 = 0, FP64 throughout, 6-level V(2,2) Chebyshev degree 4 on
+[0.1, 1.1] lambda_max (10 power iterations), GMRES coarse solve, FGMRES(30),
+stop at 1e-8 relative nonlinear residual.
+
+value:   time to solution (s per solve) with inputs resident in HBM.
+e2e:     the same through the C ABI with the initial guess copied from pinned
+         host memory and the solution copied back inside the timed region.
+extras:  FP32-preconditioned solve of the same workload (FP32 vs FP64 PC) and
+         residual-evaluation DOF/s with %HBM.
+roofline: the dominant kernel (the FP64 element-residual kernel with the fused
+         Chebyshev epilogue) timed with CUDA events on its stream during the timed
+         solves; FP64-ALU bound.
+cpu_baseline / --impl reference: the CPU oracle timed on a bounded sample.
+
+Multi-GPU (torchrun, N > 1): replicas only -- every rank solves its own
+instance, no collective on the data path; max-over-ranks time.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_ELEM = 128
+LEVELS = 6
+WORKLOAD = "nd3d_129^3_fp64_V(2,2)_cheb4_fgmres30_rtol1e-8"
+METRIC = "JFNK-MG time to 1e-8 rel. residual; residual-eval DOF/s (%HBM), FP32 vs FP64 PC"
+# FP64 operations of the sum-factorised Q1 element evaluation (element.cuh)
+ND_OPS_PER_ELEMENT = 164
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+# FP64 pipe rate measured on this machine's GB300 with a register-resident FMA
+# chain (152 SMs x ~2 FP64 ops/clk): 0.60e12 operations/s.  The profile
+# summary under profiles/ gives the command.
+FP64_OPS_PEAK = 0.60e12
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([c.strip() for c in line.split(",")])
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm = [float(r[1]) for r in self.rows if len(r) >= 9 and r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if len(r) >= 9 and r[2].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            if len(r) < 9:
+                continue
+            for k, nm in enumerate(names):
+                if r[5 + k].lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle leg
+# ---------------------------------------------------------------------------
+def oracle_sample(n=N_ELEM, reps=2):
+    """Time the oracle's FD Jacobian action (= one gradient evaluation, GE) on
+    the full 129^3 workload, and its GE count for the whole solve from its own
+    JFNK-MG solve of the same problem at 17^3 nodes (GE is level-independent,
+    Sec. 3).  Estimated oracle time to solution = t_GE(129^3) x GE_solve."""
+    import numpy as np
+
+    from oracle import fem, jfnk
+    from workloads import random_direction
+
+    t0 = time.perf_counter()
+    lvs = jfnk.build_hierarchy("nd3d", 16, 3, load=fem.mms_load(16))
+    o = jfnk.Options(nu_pre=2, nu_post=2, cheb_degree=4, rtol_newton=1e-8)
+    _, st = jfnk.newton_solve(lvs, np.zeros((17,) * 3), o)
+    t_small = time.perf_counter() - t0
+    load = fem.mms_load(n)
+    lv = jfnk.Level("nd3d", n, 0.0, None, load)
+    u = np.zeros((n + 1,) * 3)
+    Fu = lv.F(u)
+    v = random_direction(n, 3, seed=1)
+    ts = []
+    for _ in range(reps):
+        t1 = time.perf_counter()
+        jfnk.fd_jv(lv, u, Fu, v)
+        ts.append(time.perf_counter() - t1)
+    t_ge = min(ts)
+    return {"t_ge_s": t_ge, "ge_solve": st.ge, "estimate_s": t_ge * st.ge, "small_solve_s": t_small,
+            "sample": (f"{reps} oracle FD Jacobian actions (1 GE each) at 129^3 nodes, min {t_ge:.2f} s; "
+                       f"x GE={st.ge:.1f} of the oracle's own solve at 17^3 (level-independent count)")}
+
+
+def reference_arm(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    steps = []
+    for i in range(args.warmup + args.steps):
+        s = oracle_sample(reps=1)
+        if i >= args.warmup:
+            steps.append(s)
+    est = statistics.mean(s["estimate_s"] for s in steps)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": est, "unit": "s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": est * 1e3, "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (manufactured solution)",
+        "config": {"workload": WORKLOAD, "n_nodes": (N_ELEM + 1) ** 3},
+        "cpu_baseline": {"value": est, "unit": "s", "cores": 1, "kind": "oracle", "sample": steps[-1]["sample"]},
+        "e2e": {"value": est, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return reference_arm(args)
+
+    import torch
+
+    import paper_2103_13890_gb300 as jf
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    args.warmup = max(args.warmup, 3)
+    stream = torch.cuda.current_stream()
+    n = N_ELEM
+    shape = (n + 1,) * 3
+    N = (n + 1) ** 3
+
+    def make(pc):
+        o = jf.default_options(nu_pre=2, nu_post=2, cheb_degree=4, rtol_newton=1e-8,
+                               pc_dtype=jf.F32 if pc == "f32" else jf.F64,
+                               eps_mode_pc=jf.EPS_FP32 if pc == "f32" else jf.EPS_PAPER)
+        return jf.Problem("nd3d", n, LEVELS, options=o), o
+
+    p64, o64 = make("f64")
+    u = torch.zeros(shape, dtype=torch.float64, device="cuda")
+
+    def solve_once(prob):
+        u.zero_()
+        return prob.solve(u)
+
+    for _ in range(args.warmup):
+        st = solve_once(p64)
+    torch.cuda.synchronize()
+
+    # ---- timed region: K FP64 solves, inputs resident in HBM ------------------
+    sampler = ClockSampler(local)
+    sampler.start()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    jf.kernel_launches(reset=True)
+    jf.profile_enable(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    stats = []
+    for _ in range(args.steps):
+        stats.append(solve_once(p64))
+    e1.record(stream)
+    torch.cuda.synchronize()
+    launches = jf.kernel_launches()
+    prof = jf.profile_read()
+    jf.profile_enable(False)
+    ms = e0.elapsed_time(e1) / args.steps
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        dist.barrier()
+    clocks = sampler.stop()
+
+    # ---- e2e through the C ABI with host buffers -----------------------------
+    u_host = torch.zeros(shape, dtype=torch.float64).pin_memory()
+    out_host = torch.empty(shape, dtype=torch.float64).pin_memory()
+    torch.cuda.synchronize()
+    e2 = torch.cuda.Event(enable_timing=True)
+    e3 = torch.cuda.Event(enable_timing=True)
+    e2.record(stream)
+    for _ in range(args.steps):
+        u.copy_(u_host, non_blocking=True)
+        p64.solve(u)
+        out_host.copy_(u, non_blocking=True)
+    e3.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e2.elapsed_time(e3) / args.steps
+
+    # ---- FP32-preconditioned solve of the same workload -----------------------
+    p32, o32 = make("f32")
+    for _ in range(2):
+        st32 = solve_once(p32)
+    torch.cuda.synchronize()
+    e4, e5 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e4.record(stream)
+    for _ in range(args.steps):
+        st32 = solve_once(p32)
+    e5.record(stream)
+    torch.cuda.synchronize()
+    ms32 = e4.elapsed_time(e5) / args.steps
+    u32 = u.clone()
+    solve_once(p64)
+    torch.cuda.synchronize()
+    sol_diff = float((u32 - u).norm() / u.norm())
+
+    # ---- residual evaluation throughput (DOF/s, %HBM) -------------------------
+    peaks, peaks_src = load_peaks()
+    hbm = float(peaks["hbm_gbs"])
+    dof = (n - 1) ** 3
+    resid = {}
+    for dt, name in ((torch.float64, "f64"), (torch.float32, "f32")):
+        uu = torch.rand(shape, dtype=dt, device="cuda")
+        FF = torch.empty_like(uu)
+        for _ in range(3):
+            p64.residual(uu, out=FF)
+        ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 20
+        ea.record(stream)
+        for _ in range(reps):
+            p64.residual(uu, out=FF)
+        eb.record(stream)
+        torch.cuda.synchronize()
+        t = ea.elapsed_time(eb) / reps * 1e-3
+        w = 8 if name == "f64" else 4
+        byts = 3 * w * N  # read u and the load, write F
+        resid[name] = {"dof_per_s": dof / t, "ms": t * 1e3, "achieved_gbs": byts / t / 1e9,
+                       "pct_hbm": 100.0 * byts / t / 1e9 / hbm}
+
+    # ---- roofline of the dominant kernel ---------------------------------------
+    top = max(prof.items(), key=lambda kv: kv[1][1]) if prof else None
+    roof = None
+    if top:
+        name, (cnt, tot, elems) = top
+        avg_s = tot / cnt * 1e-3
+        ops = ND_OPS_PER_ELEMENT * elems
+        achieved = ops / avg_s / 1e12
+        peak = FP64_OPS_PEAK / 1e12
+        total_ms_all = sum(v[1] for v in prof.values())
+        roof = {"kernel": name, "bound": "alu", "achieved": achieved, "peak": peak,
+                "unit": "Top/s (fp64 pipe)", "frac": achieved / peak, "traffic": None,
+                "avg_launch_ms": avg_s * 1e3, "launches_in_timed_region": cnt,
+                "share_of_stencil_time": tot / total_ms_all if total_ms_all else None,
+                "peak_source": "measured fp64 pipe rate of this pool's GB300 (bench docstring)"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        s = oracle_sample(reps=2)
+        cpu = {"value": s["estimate_s"], "unit": "s", "cores": 1, "kind": "oracle", "sample": s["sample"]}
+
+    st = stats[-1]
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": ms * 1e-3, "unit": "s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic (manufactured solution, analytic load)",
+            "config": {"workload": WORKLOAD, "n_nodes": N, "unknowns": dof, "levels": LEVELS,
+                       "l2": "working set > L2 (FGMRES basis alone 31 x 17 MB)", "parallelism":
+                       "replicas" if world > 1 else "single"},
+            "solves_per_s": world * 1e3 / ms,
+            "solve": {"newton_its": st["newton_its"], "fgmres_its": st["linear_its"], "ge": st["ge"],
+                      "res_hist": st["res_hist"], "lambda_max": st["lambda_max"][:LEVELS]},
+            "fp32_pc": {"value": ms32 * 1e-3, "unit": "s", "speedup_vs_fp64": ms / ms32,
+                        "newton_its": st32["newton_its"], "fgmres_its": st32["linear_its"],
+                        "rel_diff_vs_fp64_solution": sol_diff},
+            "residual_eval": resid,
+            "e2e": {"value": e2e_ms * 1e-3, "unit": "s", "h2d_bytes_per_step": 8 * N, "d2h_bytes_per_step": 8 * N},
+            "gpu_launches": int(launches),
+            "roofline": roof,
+            "peaks": {"hbm_gbs": hbm, "source": peaks_src},
+            "cpu_baseline": cpu,
+            "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

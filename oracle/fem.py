@@ -258,6 +258,28 @@ def mms_load(n):
     return b
 
 
+def mms_load_at(n, nodes):
+    """b_i of mms_load at the given interior nodes only (array-order index
+    tuples): the same 3-point rule on the 8 elements around each node."""
+    h = 1.0 / n
+    out = []
+    for node in nodes:
+        k, j, i = (int(t) for t in node)
+        if min(i, j, k) == 0 or max(i, j, k) == n:
+            out.append(0.0)
+            continue
+        total = 0.0
+        for ez in (k - 1, k):
+            for ey in (j - 1, j):
+                for ex in (i - 1, i):
+                    loc = (i - ex, j - ey, k - ez)  # x-first local offset of the node
+                    for xi, w in gauss_points(3, rule=3):
+                        fq = mms_source((ex + xi[0]) * h, (ey + xi[1]) * h, (ez + xi[2]) * h)
+                        total += w * h ** 3 * fq * phi(loc, xi)
+        out.append(total)
+    return np.array(out)
+
+
 def node_coords(n, d):
     """Coordinate arrays (x, y[, z]) of the full node grid, in array axis order."""
     t = np.linspace(0.0, 1.0, n + 1)

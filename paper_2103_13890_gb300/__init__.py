@@ -1,0 +1,233 @@
+"""GB300 implementation of the Jacobian-free Newton-Krylov method with a
+Jacobian-free geometric multigrid preconditioner (Kothari, Kopanicakova &
+Krause, arXiv:2103.13890).
+
+Every computation runs in libjfnk.so (hand-written CUDA for sm_103a, C ABI in
+include/jfnk.h).  This module only marshals torch tensors (device memory and
+the current CUDA stream) into those calls; it has no CPU fallback and raises
+if the library is missing.
+
+    import torch, paper_2103_13890_gb300 as jf
+    p = jf.Problem("bratu2d", n_elem=64, levels=4, lam=5.0)
+    u = torch.zeros(65, 65, dtype=torch.float64, device="cuda")
+    stats = p.solve(u)            # u now holds the discrete solution
+"""
+import ctypes
+
+import torch
+
+from . import _abi
+from ._abi import BRATU2D, EPS_FP32, EPS_PAPER, F32, F64, KINDS, ND3D, NDK3D  # noqa: F401
+
+_LIB = None
+
+
+def lib():
+    global _LIB
+    if _LIB is None:
+        _LIB = _abi.load_library()
+    return _LIB
+
+
+class JFNKError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{_abi.STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+def _check(status):
+    if status != 0:
+        raise JFNKError(status, lib().jfnk_last_error().decode())
+
+
+def _stream():
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def default_options(**kw):
+    """jfnk_options with the library defaults, overridden by keyword."""
+    o = _abi.Options()
+    lib().jfnk_default_options(ctypes.byref(o))
+    for k, v in kw.items():
+        if k == "pc_dtype" and isinstance(v, torch.dtype):
+            v = F32 if v == torch.float32 else F64
+        if not hasattr(o, k):
+            raise KeyError(k)
+        setattr(o, k, v)
+    return o
+
+
+def _dtype_code(t):
+    if t.dtype == torch.float64:
+        return F64
+    if t.dtype == torch.float32:
+        return F32
+    raise TypeError(f"unsupported dtype {t.dtype}")
+
+
+def stats_dict(s):
+    L = s.newton_its
+    return {
+        "newton_its": s.newton_its, "linear_its": s.linear_its, "status": _abi.STATUS.get(s.status, s.status),
+        "converged": bool(s.converged), "res_hist": list(s.res_hist[:L + 1]),
+        "alpha_hist": list(s.alpha_hist[:L]), "lin_hist": list(s.lin_hist[:L]), "ge": s.ge,
+        "nF": list(s.nF), "lambda_max": list(s.lambda_max), "solve_ms": s.solve_ms,
+    }
+
+
+class Problem:
+    """One discretised problem on the current CUDA device with its workspace.
+
+    kind: "bratu2d" | "nd3d" | "ndk3d"; n_elem: finest elements per direction;
+    levels: multigrid levels; lam: Bratu lambda; load: optional FP64 finest
+    load vector (nd3d); kappa: FP64 per-element coefficient (ndk3d, n_elem^3).
+    options: the jfnk_options the workspace is laid out for (None: residual and
+    jvp only)."""
+
+    def __init__(self, kind, n_elem, levels, lam=0.0, load=None, kappa=None, options=None, device="cuda"):
+        self.kind = kind
+        self.d = 2 if kind == "bratu2d" else 3
+        self.n = n_elem
+        self.levels = levels
+        self.device = torch.device(device)
+        self._keep = []
+        desc = _abi.ProblemDesc()
+        desc.kind = KINDS[kind]
+        desc.n_elem = n_elem
+        desc.levels = levels
+        desc.lambda_ = lam
+        if load is not None:
+            load = load.to(self.device, torch.float64).contiguous()
+            self._keep.append(load)
+            desc.load = load.data_ptr()
+        if kappa is not None:
+            kappa = kappa.to(self.device, torch.float64).contiguous()
+            self._keep.append(kappa)
+            desc.kappa = kappa.data_ptr()
+        self._h = ctypes.c_void_p()
+        _check(lib().jfnk_problem_create(ctypes.byref(desc), ctypes.byref(self._h)))
+        self.options = options
+        opt_ref = ctypes.byref(options) if options is not None else None
+        nbytes = ctypes.c_size_t()
+        _check(lib().jfnk_workspace_size(self._h, opt_ref, ctypes.byref(nbytes)))
+        self.workspace = torch.empty(nbytes.value, dtype=torch.uint8, device=self.device)
+        _check(lib().jfnk_set_workspace(self._h, opt_ref, _ptr(self.workspace), nbytes.value, _stream()))
+
+    def shape(self, level=None):
+        lv = self.levels - 1 if level is None else level
+        m = (self.n >> (self.levels - 1 - lv)) + 1
+        return (m,) * self.d
+
+    def _lv(self, level):
+        return self.levels - 1 if level is None else level
+
+    def residual(self, u, level=None, out=None):
+        """F(u) on a level (finest: A(u) - load; coarse: A(u))."""
+        lv = self._lv(level)
+        out = torch.empty_like(u) if out is None else out
+        _check(lib().jfnk_residual(self._h, lv, _dtype_code(u), _ptr(u), _ptr(out), _stream()))
+        return out
+
+    def jvp(self, u, Fu, v, level=None, eps=0.0, eps_mode=EPS_PAPER, out=None):
+        """(F(u + eps v) - F(u)) / eps with F(u) = Fu; eps <= 0 selects eps_mode."""
+        lv = self._lv(level)
+        out = torch.empty_like(u) if out is None else out
+        _check(lib().jfnk_jvp(self._h, lv, _dtype_code(u), _ptr(u), _ptr(Fu), _ptr(v), _ptr(out),
+                              float(eps), int(eps_mode), _stream()))
+        return out
+
+    def mg_setup(self, u, newton_step=0, options=None):
+        o = options or self.options
+        _check(lib().jfnk_mg_setup(self._h, ctypes.byref(o), _ptr(u), int(newton_step), _stream()))
+
+    def mg_vcycle(self, b, out=None, options=None):
+        o = options or self.options
+        out = torch.empty_like(b) if out is None else out
+        _check(lib().jfnk_mg_vcycle(self._h, ctypes.byref(o), _ptr(b), _ptr(out), _stream()))
+        return out
+
+    def transfer(self, op, x, level=None, out=None):
+        """op: "restrict" | "project" (level -> level-1) or "prolong_add" (out(level) += I x)."""
+        lv = self._lv(level)
+        code = {"restrict": _abi.RESTRICT, "prolong_add": _abi.PROLONG_ADD, "project": _abi.PROJECT}[op]
+        if out is None:
+            if code == _abi.PROLONG_ADD:
+                raise ValueError("prolong_add accumulates into out")
+            out = torch.empty(self.shape(lv - 1), dtype=x.dtype, device=x.device)
+        _check(lib().jfnk_transfer(self._h, code, lv, _dtype_code(x), _ptr(x), _ptr(out), _stream()))
+        return out
+
+    def smooth(self, b, s, level=None, nu=1, s_is_zero=False, options=None):
+        o = options or self.options
+        _check(lib().jfnk_smooth(self._h, ctypes.byref(o), self._lv(level), _ptr(b), _ptr(s), int(nu),
+                                 1 if s_is_zero else 0, _stream()))
+        return s
+
+    def coarse_solve(self, b, out=None, options=None):
+        o = options or self.options
+        out = torch.empty_like(b) if out is None else out
+        _check(lib().jfnk_coarse_solve(self._h, ctypes.byref(o), _ptr(b), _ptr(out), _stream()))
+        return out
+
+    def level_info(self, level):
+        lam, x1, x2 = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        _check(lib().jfnk_level_info(self._h, level, ctypes.byref(lam), ctypes.byref(x1), ctypes.byref(x2),
+                                     _stream()))
+        return {"lambda_max": lam.value, "sum_abs_x": x1.value, "norm2_x": x2.value}
+
+    def level_vector(self, level, which):
+        """which: "x" | "Ax" | "power" (preconditioner precision)."""
+        dt = torch.float32 if self.options.pc_dtype == F32 else torch.float64
+        out = torch.empty(self.shape(level), dtype=dt, device=self.device)
+        code = {"x": 0, "Ax": 1, "power": 2}[which]
+        _check(lib().jfnk_level_vector(self._h, level, code, _ptr(out), _stream()))
+        return out
+
+    def solve(self, u, options=None, check=True):
+        """Inexact JFNK solve in place on u (FP64, full node grid).  Returns stats."""
+        o = options or self.options
+        st = _abi.Stats()
+        status = lib().jfnk_solve(self._h, ctypes.byref(o), _ptr(u), ctypes.byref(st), _stream())
+        if check:
+            _check(status)
+        d = stats_dict(st)
+        d["status_code"] = status
+        return d
+
+    def close(self):
+        if self._h:
+            lib().jfnk_problem_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def kernel_launches(reset=False):
+    return lib().jfnk_kernel_launches(1 if reset else 0)
+
+
+def profile_enable(on=True):
+    lib().jfnk_profile_enable(1 if on else 0)
+
+
+def profile_read(max_classes=256):
+    """{class name: (launches, total_ms, elements_per_launch)} of the event profile."""
+    nl = 96
+    names = ctypes.create_string_buffer(max_classes * nl)
+    cnt = (ctypes.c_longlong * max_classes)()
+    ms = (ctypes.c_double * max_classes)()
+    work = (ctypes.c_double * max_classes)()
+    n = lib().jfnk_profile_read(max_classes, names, nl, cnt, ms, work)
+    out = {}
+    for i in range(min(n, max_classes)):
+        name = names.raw[i * nl:(i + 1) * nl].split(b"\0", 1)[0].decode()
+        out[name] = (cnt[i], ms[i], work[i])
+    return out

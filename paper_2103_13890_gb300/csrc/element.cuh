@@ -1,0 +1,186 @@
+// Element arithmetic of the Q1 residuals with the 2^d-point Gauss rule.
+//
+// The element integrals are the ones of the problem definitions (Sec. 3 and
+// the configured workloads): for a Q1 element with nodal values u_abc
+//   R_abc = sum_q w_q [ c(u_q) grad u_q . grad phi_abc(q) (+ source term) ]
+// with Gauss points 1/2 +- 1/(2 sqrt 3) per direction.
+//
+// Evaluation order (exact reformulation, rounding differs from a quadrature
+// loop):  a 1D Q1 function at the two Gauss points is m +- A delta with
+// m = (u0+u1)/2, delta = (u1-u0)/2 and A = 1/sqrt 3, and its derivative is
+// 2 delta / h.  So the nodal values are first turned into "modal"
+// coefficients by sum/difference butterflies in each direction, the values and
+// gradients at all Gauss points follow from 2-point butterflies of the scaled
+// modes, and the test-function side is the transpose of the same chain.  In
+// 3D this costs 164 floating-point operations per element for nonlinear
+// diffusion (a direct quadrature loop needs ~500), which matters because FP64
+// throughput on GB300 is ~1/61 of FP32.
+#pragma once
+
+#ifndef __CUDACC__
+#define __host__
+#define __device__
+#define __forceinline__ inline
+#endif
+
+namespace jfnk {
+
+// 2-point butterfly over two sign variables, forward:
+//   out[i][j] = v00 + s_i v10 + s_j v01 + s_i s_j v11,  s_0 = -1, s_1 = +1
+template <typename T>
+__host__ __device__ __forceinline__ void h2_fwd(T v00, T v10, T v01, T v11, T out[2][2]) {
+    T t0p = v00 + v01, t0m = v00 - v01;
+    T t1p = v10 + v11, t1m = v10 - v11;
+    out[1][1] = t0p + t1p;
+    out[0][1] = t0p - t1p;
+    out[1][0] = t0m + t1m;
+    out[0][0] = t0m - t1m;
+}
+
+// transpose: w_pq = sum_{i,j} s_i^p s_j^q F[i][j]
+template <typename T>
+__host__ __device__ __forceinline__ void h2_adj(const T F[2][2], T& w00, T& w10, T& w01, T& w11) {
+    T S0 = F[1][0] + F[0][0], S1 = F[1][1] + F[0][1];
+    T D0 = F[1][0] - F[0][0], D1 = F[1][1] - F[0][1];
+    w00 = S1 + S0;
+    w01 = S1 - S0;
+    w10 = D1 + D0;
+    w11 = D1 - D0;
+}
+
+// ---------------------------------------------------------------------------
+// 3D nonlinear diffusion element.
+//   u[8]: nodal values, index a + 2b + 4c for offsets (a, b, c) in (x, y, z)
+//   kap:  per-element coefficient (1 for the plain problem)
+//   r[8]: sum_q (1/ (3h/16)) * w_q * kap (1+u_q^2) grad u_q . grad phi_abc(q),
+//         i.e. the element residual divided by 3h/16, which the caller applies
+//         once per node.
+// ---------------------------------------------------------------------------
+template <typename T, bool KAPPA>
+__host__ __device__ __forceinline__ void elem_nd3(const T u[8], T kap, T r[8]) {
+    const T A1 = T(0.57735026918962576451);   // 1/sqrt(3)
+    const T A2 = T(0.33333333333333333333);   // 1/3
+    const T A3 = T(0.19245008972987525484);   // 1/(3 sqrt 3)
+    // modal transform M' = T' (x) T' (x) T' u, T' = [[1,1],[-1,1]]  (24 ops)
+    T p0 = u[0] + u[1], q0 = u[1] - u[0];
+    T p1 = u[2] + u[3], q1 = u[3] - u[2];
+    T p2 = u[4] + u[5], q2 = u[5] - u[4];
+    T p3 = u[6] + u[7], q3 = u[7] - u[6];
+    T a00 = p0 + p1, a01 = p1 - p0, b00 = p2 + p3, b01 = p3 - p2;  // x-mode 0
+    T a10 = q0 + q1, a11 = q1 - q0, b10 = q2 + q3, b11 = q3 - q2;  // x-mode 1
+    // S_pqr = M'_pqr A^(p+q+r) / 8  (8 ops)
+    T S000 = (a00 + b00) * T(0.125);
+    T S001 = (b00 - a00) * (A1 * T(0.125));
+    T S010 = (a01 + b01) * (A1 * T(0.125));
+    T S011 = (b01 - a01) * (A2 * T(0.125));
+    T S100 = (a10 + b10) * (A1 * T(0.125));
+    T S101 = (b10 - a10) * (A2 * T(0.125));
+    T S110 = (a11 + b11) * (A2 * T(0.125));
+    T S111 = (b11 - a11) * (A3 * T(0.125));
+    // values and (scaled) gradients at the Gauss points (40 ops)
+    T P0[2][2], GX[2][2], GY[2][2], GZ[2][2];
+    h2_fwd(S000, S010, S001, S011, P0);  // [sy][sz]
+    h2_fwd(S100, S110, S101, S111, GX);  // [sy][sz]  d/dx = 2/(hA) GX
+    h2_fwd(S010, S110, S011, S111, GY);  // [sx][sz]
+    h2_fwd(S001, S101, S011, S111, GZ);  // [sx][sy]
+    // coefficient c = kap (1 + u^2) at the 8 points, index [sx][sy][sz]
+    T c[2][2][2];
+#pragma unroll
+    for (int j = 0; j < 2; ++j)
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            T up = P0[j][k] + GX[j][k];
+            T um = P0[j][k] - GX[j][k];
+            if (KAPPA) {
+                c[1][j][k] = (kap * up) * up + kap;
+                c[0][j][k] = (kap * um) * um + kap;
+            } else {
+                c[1][j][k] = up * up + T(1);
+                c[0][j][k] = um * um + T(1);
+            }
+        }
+    // sum the flux over the direction its gradient factor does not depend on
+    T FX[2][2], FY[2][2], FZ[2][2];
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            FX[i][j] = GX[i][j] * (c[1][i][j] + c[0][i][j]);  // [sy][sz]
+            FY[i][j] = GY[i][j] * (c[i][1][j] + c[i][0][j]);  // [sx][sz]
+            FZ[i][j] = GZ[i][j] * (c[i][j][1] + c[i][j][0]);  // [sx][sy]
+        }
+    T X00, X10, X01, X11, Y00, Y10, Y01, Y11, Z00, Z10, Z01, Z11;
+    h2_adj(FX, X00, X10, X01, X11);  // X_qr
+    h2_adj(FY, Y00, Y10, Y01, Y11);  // Y_pr
+    h2_adj(FZ, Z00, Z10, Z01, Z11);  // Z_pq
+    // test-function modes, scaled by A^(p+q+r) (12 ops)
+    T R100 = X00 * A1, R010 = Y00 * A1, R001 = Z00 * A1;
+    T R110 = (X10 + Y10) * A2;
+    T R101 = (X01 + Z10) * A2;
+    T R011 = (Y01 + Z01) * A2;
+    T R111 = (X11 + Y11 + Z11) * A3;
+    // transpose of the modal transform (R000 = 0)  (24 ops)
+    // z pass: (mode r) -> (c)
+    T e00_0 = -R001, e00_1 = R001;            // (p,q) = (0,0)
+    T e01_0 = R010 - R011, e01_1 = R010 + R011;  // (0,1)
+    T e10_0 = R100 - R101, e10_1 = R100 + R101;  // (1,0)
+    T e11_0 = R110 - R111, e11_1 = R110 + R111;  // (1,1)
+    // y pass: (mode q) -> (b)
+    T f0_00 = e00_0 - e01_0, f0_10 = e00_0 + e01_0;  // p=0, (b,c)=(0,0),(1,0)
+    T f0_01 = e00_1 - e01_1, f0_11 = e00_1 + e01_1;  // p=0, (0,1),(1,1)
+    T f1_00 = e10_0 - e11_0, f1_10 = e10_0 + e11_0;
+    T f1_01 = e10_1 - e11_1, f1_11 = e10_1 + e11_1;
+    // x pass: (mode p) -> (a)
+    r[0] = f0_00 - f1_00; r[1] = f0_00 + f1_00;
+    r[2] = f0_10 - f1_10; r[3] = f0_10 + f1_10;
+    r[4] = f0_01 - f1_01; r[5] = f0_01 + f1_01;
+    r[6] = f0_11 - f1_11; r[7] = f0_11 + f1_11;
+}
+
+// ---------------------------------------------------------------------------
+// 2D Bratu element (Sec. 3).
+//   u[4]: nodal values, index a + 2b
+//   lh:   lambda h^2 / 16
+//   r[4]: int_e grad u_h . grad phi_ab - lambda exp(u_h) phi_ab   (exact scale)
+// With M' = T' (x) T' u the gradient part in modal form is
+// (0, M'_10/4, M'_01/4, M'_11/6) and the source part is
+// -(lambda h^2/16) A^(p+q) sum_q s_x^p s_y^q exp(u_q).
+// ---------------------------------------------------------------------------
+template <typename T>
+__host__ __device__ __forceinline__ T exp_t(T x);
+template <>
+__host__ __device__ __forceinline__ double exp_t<double>(double x) { return exp(x); }
+template <>
+__host__ __device__ __forceinline__ float exp_t<float>(float x) { return expf(x); }
+
+template <typename T>
+__host__ __device__ __forceinline__ void elem_bratu2(const T u[4], T lh, T r[4]) {
+    const T A1 = T(0.57735026918962576451);
+    const T A2 = T(0.33333333333333333333);
+    T p0 = u[0] + u[1], q0 = u[1] - u[0];
+    T p1 = u[2] + u[3], q1 = u[3] - u[2];
+    T M00 = p0 + p1, M01 = p1 - p0, M10 = q0 + q1, M11 = q1 - q0;
+    T S00 = M00 * T(0.25), S10 = M10 * (A1 * T(0.25));
+    T S01 = M01 * (A1 * T(0.25)), S11 = M11 * (A2 * T(0.25));
+    T U[2][2];  // [sx][sy]
+    h2_fwd(S00, S10, S01, S11, U);
+    T E[2][2];
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 2; ++j) E[i][j] = exp_t<T>(U[i][j]);
+    T E00, E10, E01, E11;
+    h2_adj(E, E00, E10, E01, E11);
+    T la1 = lh * A1, la2 = lh * A2;
+    T R00 = -lh * E00;
+    T R10 = M10 * T(0.25) - la1 * E10;
+    T R01 = M01 * T(0.25) - la1 * E01;
+    T R11 = M11 * T(0.16666666666666666667) - la2 * E11;
+    // transpose of the modal transform
+    T g0_0 = R00 - R01, g0_1 = R00 + R01;  // p=0, b=0/1
+    T g1_0 = R10 - R11, g1_1 = R10 + R11;  // p=1
+    r[0] = g0_0 - g1_0; r[1] = g0_0 + g1_0;
+    r[2] = g0_1 - g1_1; r[3] = g0_1 + g1_1;
+}
+
+}  // namespace jfnk

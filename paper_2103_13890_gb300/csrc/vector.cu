@@ -1,0 +1,455 @@
+// Vector kernels: deterministic reductions (fixed grids, last-block
+// completion), BLAS-1 updates, casts and the power-method start vector.
+#include "reduce.cuh"
+#include "vector.cuh"
+
+namespace jfnk {
+
+constexpr int kVecThreads = 256;
+constexpr int kVecBlocks = 304;  // 2 x 152 SMs; fixed so sums are reproducible
+
+static int vec_blocks(long long len) {
+    long long b = (len + kVecThreads - 1) / kVecThreads;
+    return (int)(b < kVecBlocks ? (b < 1 ? 1 : b) : kVecBlocks);
+}
+
+__device__ __forceinline__ bool grid_inner(const Grid& g, long long i) {
+    const long long x = i % g.sy;
+    const long long yz = i / g.sy;
+    const long long y = yz % g.ny;
+    const long long z = yz / g.ny;
+    bool in = x > 0 && x < g.nx - 1 && y > 0 && y < g.ny - 1;
+    if (g.d == 3) in = in && z > 0 && z < g.nz - 1;
+    return in;
+}
+
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void masked_stat_kernel(Grid g, const T* x, int what, double* out, double* partials,
+                                   unsigned int* counter, EpsParams ep, EpsSlot* slot, double* norm_out) {
+    __shared__ double sm[32];
+    double acc = 0.0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < g.size;
+         i += (long long)gridDim.x * blockDim.x) {
+        if (!grid_inner(g, i)) continue;
+        double v = (double)x[i];
+        acc += (what == 0) ? fabs(v) : v * v;
+    }
+    double bs = block_sum(acc, sm);
+    double tot = 0.0;
+    if (grid_sum_last(bs, partials, counter, &tot, sm) && threadIdx.x == 0) {
+        double r = (what == 0) ? tot : sqrt(tot);
+        if (out) *out = r;
+        if (norm_out) *norm_out = r;
+        if (slot) {
+            double e = eps_formula(ep.mode, ep.n_unknowns, *ep.xstat, r);
+            double inv = e > 0.0 ? 1.0 / e : 0.0;
+            slot->e = e;
+            slot->inv = inv;
+            slot->ef = (float)e;
+            slot->invf = (float)inv;
+        }
+    }
+}
+
+template <typename T>
+jfnk_status masked_stat(const Grid& g, const T* x, int what, double* out, RedScratch* red, cudaStream_t st) {
+    EpsParams ep{};
+    masked_stat_kernel<T><<<vec_blocks(g.size), kVecThreads, 0, st>>>(g, x, what, out, red->partial,
+                                                                      &red->counter[0], ep, nullptr, nullptr);
+    JFNK_LAUNCH_CHECK();
+    return JFNK_OK;
+}
+
+template <typename T>
+jfnk_status norm_to_eps(const Grid& g, const T* v, const EpsParams& ep, EpsSlot* slot, double* norm_out,
+                        RedScratch* red, cudaStream_t st) {
+    masked_stat_kernel<T><<<vec_blocks(g.size), kVecThreads, 0, st>>>(g, v, 1, nullptr, red->partial,
+                                                                      &red->counter[0], ep, slot, norm_out);
+    JFNK_LAUNCH_CHECK();
+    return JFNK_OK;
+}
+
+template jfnk_status masked_stat<float>(const Grid&, const float*, int, double*, RedScratch*, cudaStream_t);
+template jfnk_status masked_stat<double>(const Grid&, const double*, int, double*, RedScratch*, cudaStream_t);
+template jfnk_status norm_to_eps<float>(const Grid&, const float*, const EpsParams&, EpsSlot*, double*,
+                                        RedScratch*, cudaStream_t);
+template jfnk_status norm_to_eps<double>(const Grid&, const double*, const EpsParams&, EpsSlot*, double*,
+                                         RedScratch*, cudaStream_t);
+
+// ---------------------------------------------------------------------------
+// multi-dot: blockIdx.y selects a group of 8 vectors
+constexpr int kDotGroup = 8;
+__global__ void multi_dot_kernel(const double* __restrict__ w, const double* __restrict__ V, long long ld,
+                                 long long len, int m, double* h, double* partials, unsigned int* counter) {
+    __shared__ double sm[kDotGroup][32];
+    __shared__ int s_last;
+    const int g0 = blockIdx.y * kDotGroup;
+    const int ng = min(kDotGroup, m - g0);
+    double acc[kDotGroup];
+#pragma unroll
+    for (int k = 0; k < kDotGroup; ++k) acc[k] = 0.0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < len;
+         i += (long long)gridDim.x * blockDim.x) {
+        const double wi = w[i];
+#pragma unroll
+        for (int k = 0; k < kDotGroup; ++k)
+            if (k < ng) acc[k] += wi * V[(long long)(g0 + k) * ld + i];
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < kDotGroup; ++k) {
+        double v = warp_sum(acc[k]);
+        if (lane == 0) sm[k][wid] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < kDotGroup && threadIdx.x < ng) {
+        double s = 0.0;
+        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) s += sm[threadIdx.x][q];
+        partials[(long long)(g0 + threadIdx.x) * gridDim.x + blockIdx.x] = s;
+        __threadfence();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        unsigned int nb = gridDim.x * gridDim.y;
+        unsigned int prev = atomicAdd(counter, 1u);
+        s_last = (prev == nb - 1) ? 1 : 0;
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    // last block: each warp sums one vector's partials in order
+    for (int k = wid; k < m; k += blockDim.x >> 5) {
+        double s = 0.0;
+        for (int b = lane; b < (int)gridDim.x; b += 32) s += __ldcg(&partials[(long long)k * gridDim.x + b]);
+        s = warp_sum(s);
+        if (lane == 0) h[k] = s;
+    }
+    if (threadIdx.x == 0) *counter = 0u;
+}
+
+jfnk_status multi_dot(const double* w, const double* V, long long ld, long long len, int m, double* h,
+                      double* partials, unsigned int* counter, cudaStream_t st) {
+    if (m <= 0) return JFNK_OK;
+    int gx = vec_blocks(len);
+    if (gx > kDotBlocks) gx = kDotBlocks;
+    dim3 grid(gx, (m + kDotGroup - 1) / kDotGroup);
+    multi_dot_kernel<<<grid, kVecThreads, 0, st>>>(w, V, ld, len, m, h, partials, counter);
+    JFNK_LAUNCH_CHECK();
+    return JFNK_OK;
+}
+
+__global__ void multi_axpy_sub_kernel(double* __restrict__ w, const double* __restrict__ V, long long ld,
+                                      long long len, int m, const double* __restrict__ h) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < len;
+         i += (long long)gridDim.x * blockDim.x) {
+        double acc = w[i];
+        for (int k = 0; k < m; ++k) acc -= h[k] * V[(long long)k * ld + i];
+        w[i] = acc;
+    }
+}
+
+jfnk_status multi_axpy_sub(double* w, const double* V, long long ld, long long len, int m, const double* h,
+                           cudaStream_t st) {
+    if (m <= 0) return JFNK_OK;
+    multi_axpy_sub_kernel<<<vec_blocks(len), kVecThreads, 0, st>>>(w, V, ld, len, m, h);
+    JFNK_LAUNCH_CHECK();
+    return JFNK_OK;
+}
+
+__global__ void sumsq_kernel(const double* __restrict__ w, long long len, double* nrm_out, double* partials,
+                             unsigned int* counter) {
+    __shared__ double sm[32];
+    double acc = 0.0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < len;
+         i += (long long)gridDim.x * blockDim.x) {
+        double v = w[i];
+        acc += v * v;
+    }
+    double bs = block_sum(acc, sm);
+    double tot = 0.0;
+    if (grid_sum_last(bs, partials, counter, &tot, sm) && threadIdx.x == 0) *nrm_out = sqrt(tot);
+}
+
+__global__ void scale_inv_kernel(double* __restrict__ y, const double* __restrict__ x, long long len,
+                                 const double* nrm) {
+    const double n = *nrm;
+    const double s = n > 0.0 ? 1.0 / n : 0.0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < len;
+         i += (long long)gridDim.x * blockDim.x)
+        y[i] = x[i] * s;
+}
+
+jfnk_status normalize(double* w, long long len, double* nrm_out, double* partials, unsigned int* counter,
+                      cudaStream_t st) {
+    sumsq_kernel<<<vec_blocks(len), kVecThreads, 0, st>>>(w, len, nrm_out, partials, counter);
+    JFNK_LAUNCH_CHECK();
+    scale_inv_kernel<<<vec_blocks(len), kVecThreads, 0, st>>>(w, w, len, nrm_out);
+    JFNK_LAUNCH_CHECK();
+    return JFNK_OK;
+}
+
+jfnk_status scale_by_inv(double* y, const double* x, long long len, const double* nrm, cudaStream_t st) {
+    scale_inv_kernel<<<vec_blocks(len), kVecThreads, 0, st>>>(y, x, len, nrm);
+    JFNK_LAUNCH_CHECK();
+    return JFNK_OK;
+}
+
+// ---------------------------------------------------------------------------
+template <typename TZ>
+__global__ void combine_kernel(double* __restrict__ x, const TZ* __restrict__ Z, long long ld, long long len,
+                               int m, const double* __restrict__ c) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < len;
+         i += (long long)gridDim.x * blockDim.x) {
+        double acc = x[i];
+        for (int k = 0; k < m; ++k) acc += c[k] * (double)Z[(long long)k * ld + i];
+        x[i] = acc;
+    }
+}
+
+template <typename TZ>
+jfnk_status combine(double* x, const TZ* Z, long long ld, long long len, int m, const double* c, cudaStream_t st) {
+    if (m <= 0) return JFNK_OK;
+    combine_kernel<TZ><<<vec_blocks(len), kVecThreads, 0, st>>>(x, Z, ld, len, m, c);
+    JFNK_LAUNCH_CHECK();
+    return JFNK_OK;
+}
+template jfnk_status combine<float>(double*, const float*, long long, long long, int, const double*, cudaStream_t);
+template jfnk_status combine<double>(double*, const double*, long long, long long, int, const double*, cudaStream_t);
+
+template <typename T>
+__global__ void axpby_kernel(T* __restrict__ y, const T* __restrict__ x, T a, T b, long long len) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < len;
+         i += (long long)gridDim.x * blockDim.x)
+        y[i] = a * x[i] + b * y[i];
+}
+
+template <typename T>
+jfnk_status axpby(T* y, const T* x, double a, double b, long long len, cudaStream_t st) {
+    axpby_kernel<T><<<vec_blocks(len), kVecThreads, 0, st>>>(y, x, (T)a, (T)b, len);
+    JFNK_LAUNCH_CHECK();
+    return JFNK_OK;
+}
+template jfnk_status axpby<float>(float*, const float*, double, double, long long, cudaStream_t);
+template jfnk_status axpby<double>(double*, const double*, double, double, long long, cudaStream_t);
+
+__global__ void add_scaled_kernel(double* __restrict__ z, const double* __restrict__ x, double a,
+                                  const double* __restrict__ y, long long len) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < len;
+         i += (long long)gridDim.x * blockDim.x)
+        z[i] = x[i] + a * y[i];
+}
+
+jfnk_status add_scaled(double* z, const double* x, double a, const double* y, long long len, cudaStream_t st) {
+    add_scaled_kernel<<<vec_blocks(len), kVecThreads, 0, st>>>(z, x, a, y, len);
+    JFNK_LAUNCH_CHECK();
+    return JFNK_OK;
+}
+
+template <typename TO, typename TI>
+__global__ void cast_kernel(TO* __restrict__ y, const TI* __restrict__ x, long long len) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < len;
+         i += (long long)gridDim.x * blockDim.x)
+        y[i] = (TO)x[i];
+}
+
+template <typename TO, typename TI>
+jfnk_status cast_copy(TO* y, const TI* x, long long len, cudaStream_t st) {
+    cast_kernel<TO, TI><<<vec_blocks(len), kVecThreads, 0, st>>>(y, x, len);
+    JFNK_LAUNCH_CHECK();
+    return JFNK_OK;
+}
+template jfnk_status cast_copy<float, double>(float*, const double*, long long, cudaStream_t);
+template jfnk_status cast_copy<double, float>(double*, const float*, long long, cudaStream_t);
+template jfnk_status cast_copy<double, double>(double*, const double*, long long, cudaStream_t);
+template jfnk_status cast_copy<float, float>(float*, const float*, long long, cudaStream_t);
+
+template <typename TO, typename TI>
+__global__ void cast_scale_interior_kernel(TO* __restrict__ y, const TI* __restrict__ x, double a, Grid g) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < g.size;
+         i += (long long)gridDim.x * blockDim.x)
+        y[i] = grid_inner(g, i) ? (TO)(a * (double)x[i]) : TO(0);
+}
+
+template <typename TO, typename TI>
+jfnk_status cast_scale_interior(TO* y, const TI* x, double a, const Grid& g, cudaStream_t st) {
+    cast_scale_interior_kernel<TO, TI><<<vec_blocks(g.size), kVecThreads, 0, st>>>(y, x, a, g);
+    JFNK_LAUNCH_CHECK();
+    return JFNK_OK;
+}
+template jfnk_status cast_scale_interior<float, double>(float*, const double*, double, const Grid&, cudaStream_t);
+template jfnk_status cast_scale_interior<double, double>(double*, const double*, double, const Grid&, cudaStream_t);
+template jfnk_status cast_scale_interior<double, float>(double*, const float*, double, const Grid&, cudaStream_t);
+template jfnk_status cast_scale_interior<float, float>(float*, const float*, double, const Grid&, cudaStream_t);
+
+template <typename T>
+__global__ void add_inplace_kernel(T* __restrict__ s, const T* __restrict__ d, long long len) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < len;
+         i += (long long)gridDim.x * blockDim.x)
+        s[i] += d[i];
+}
+
+template <typename T>
+jfnk_status add_inplace(T* s, const T* d, long long len, cudaStream_t st) {
+    add_inplace_kernel<T><<<vec_blocks(len), kVecThreads, 0, st>>>(s, d, len);
+    JFNK_LAUNCH_CHECK();
+    return JFNK_OK;
+}
+template jfnk_status add_inplace<float>(float*, const float*, long long, cudaStream_t);
+template jfnk_status add_inplace<double>(double*, const double*, long long, cudaStream_t);
+
+// ---------------------------------------------------------------------------
+// SplitMix64 (Steele, Lea & Flood 2014): state advances by GAMMA, output is the
+// 64-bit finaliser of the state.  Counter form: output c of stream k is
+// finaliser(k + (c+1) GAMMA).
+__device__ __forceinline__ uint64_t splitmix_finalise(uint64_t z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+
+template <typename T>
+__global__ void splitmix_kernel(Grid g, T* v, uint64_t key) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < g.size;
+         i += (long long)gridDim.x * blockDim.x) {
+        T val = T(0);
+        if (grid_inner(g, i)) {
+            uint64_t z = splitmix_finalise(key + ((uint64_t)i + 1ULL) * 0x9E3779B97F4A7C15ULL);
+            double u = (double)(z >> 11) * 0x1.0p-53;
+            val = (T)(u * 2.0 - 1.0);
+        }
+        v[i] = val;
+    }
+}
+
+template <typename T>
+jfnk_status splitmix_start(const Grid& g, T* v, uint64_t seed, int level, cudaStream_t st) {
+    const uint64_t key = seed + (uint64_t)level * 0xD1B54A32D192ED03ULL;
+    splitmix_kernel<T><<<vec_blocks(g.size), kVecThreads, 0, st>>>(g, v, key);
+    JFNK_LAUNCH_CHECK();
+    return JFNK_OK;
+}
+template jfnk_status splitmix_start<float>(const Grid&, float*, uint64_t, int, cudaStream_t);
+template jfnk_status splitmix_start<double>(const Grid&, double*, uint64_t, int, cudaStream_t);
+
+// ---------------------------------------------------------------------------
+__global__ void cheb_table_kernel(const double* lam, double lo, double hi, int degree, ChebTable* t, int* status) {
+    const double l = *lam;
+    if (!(l > 0.0) || !isfinite(l)) {
+        if (status) atomicOr(status, 2);
+    }
+    double theta, c1, c2;
+    cheb_coeffs(l, lo, hi, 0, theta, c1, c2);
+    t->theta_inv = 1.0 / theta;
+    t->theta_invf = (float)(1.0 / theta);
+    for (int i = 0; i < degree && i < kMaxChebDegree; ++i) {
+        cheb_coeffs(l, lo, hi, i, theta, c1, c2);
+        t->c1[i] = c1;
+        t->c2[i] = c2;
+        t->c1f[i] = (float)c1;
+        t->c2f[i] = (float)c2;
+    }
+}
+
+jfnk_status cheb_table(const double* lam, double lo, double hi, int degree, ChebTable* t, int* status,
+                       cudaStream_t st) {
+    cheb_table_kernel<<<1, 1, 0, st>>>(lam, lo, hi, degree, t, status);
+    JFNK_LAUNCH_CHECK();
+    return JFNK_OK;
+}
+
+__global__ void copy_scalar_kernel(double* d, const double* s) { *d = *s; }
+jfnk_status copy_scalar(double* dst, const double* src, cudaStream_t st) {
+    copy_scalar_kernel<<<1, 1, 0, st>>>(dst, src);
+    JFNK_LAUNCH_CHECK();
+    return JFNK_OK;
+}
+
+}  // namespace jfnk
+
+namespace jfnk {
+
+template <typename T>
+__global__ void cheb_start_zero_kernel(Grid g, const T* __restrict__ b, T* __restrict__ r, T* __restrict__ d,
+                                       const ChebTable* cheb, EpsParams ep, EpsSlot* slot, double* partials,
+                                       unsigned int* counter) {
+    __shared__ double sm[32];
+    const double ti = cheb->theta_inv;
+    double acc = 0.0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < g.size;
+         i += (long long)gridDim.x * blockDim.x) {
+        const bool in = grid_inner(g, i);
+        const T bv = in ? b[i] : T(0);
+        const T dv = (T)((double)bv * ti);
+        r[i] = bv;
+        d[i] = dv;
+        acc += (double)dv * (double)dv;
+    }
+    double bs = block_sum(acc, sm);
+    double tot = 0.0;
+    if (grid_sum_last(bs, partials, counter, &tot, sm) && threadIdx.x == 0) {
+        double e = eps_formula(ep.mode, ep.n_unknowns, *ep.xstat, sqrt(tot));
+        double inv = e > 0.0 ? 1.0 / e : 0.0;
+        slot->e = e;
+        slot->inv = inv;
+        slot->ef = (float)e;
+        slot->invf = (float)inv;
+    }
+}
+
+template <typename T>
+jfnk_status cheb_start_zero(const Grid& g, const T* b, T* r, T* d, const ChebTable* cheb, const EpsParams& ep,
+                            EpsSlot* slot, RedScratch* red, cudaStream_t st) {
+    cheb_start_zero_kernel<T><<<vec_blocks(g.size), kVecThreads, 0, st>>>(g, b, r, d, cheb, ep, slot, red->partial,
+                                                                          &red->counter[0]);
+    JFNK_LAUNCH_CHECK();
+    return JFNK_OK;
+}
+template jfnk_status cheb_start_zero<float>(const Grid&, const float*, float*, float*, const ChebTable*,
+                                            const EpsParams&, EpsSlot*, RedScratch*, cudaStream_t);
+template jfnk_status cheb_start_zero<double>(const Grid&, const double*, double*, double*, const ChebTable*,
+                                             const EpsParams&, EpsSlot*, RedScratch*, cudaStream_t);
+
+template <typename T>
+__global__ void scale_inplace_inv_kernel(T* v, long long len, const double* nrm) {
+    const double n = *nrm;
+    const T s = (T)(n > 0.0 ? 1.0 / n : 0.0);
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < len;
+         i += (long long)gridDim.x * blockDim.x)
+        v[i] *= s;
+}
+
+template <typename T>
+jfnk_status scale_inplace_inv(T* v, long long len, const double* nrm, cudaStream_t st) {
+    scale_inplace_inv_kernel<T><<<vec_blocks(len), kVecThreads, 0, st>>>(v, len, nrm);
+    JFNK_LAUNCH_CHECK();
+    return JFNK_OK;
+}
+template jfnk_status scale_inplace_inv<float>(float*, long long, const double*, cudaStream_t);
+template jfnk_status scale_inplace_inv<double>(double*, long long, const double*, cudaStream_t);
+
+__global__ void set_eps_kernel(EpsSlot* s, double e) {
+    double inv = e > 0.0 ? 1.0 / e : 0.0;
+    s->e = e;
+    s->inv = inv;
+    s->ef = (float)e;
+    s->invf = (float)inv;
+}
+jfnk_status set_eps(EpsSlot* slot, double e, cudaStream_t st) {
+    set_eps_kernel<<<1, 1, 0, st>>>(slot, e);
+    JFNK_LAUNCH_CHECK();
+    return JFNK_OK;
+}
+
+__global__ void ratio_kernel(double* lam, const double* a, const double* b) {
+    const double bb = *b;
+    *lam = bb > 0.0 ? *a / bb : 0.0;
+}
+jfnk_status ratio_scalar(double* lam, const double* a, const double* b, cudaStream_t st) {
+    ratio_kernel<<<1, 1, 0, st>>>(lam, a, b);
+    JFNK_LAUNCH_CHECK();
+    return JFNK_OK;
+}
+
+}  // namespace jfnk

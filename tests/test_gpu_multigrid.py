@@ -1,0 +1,164 @@
+"""GPU parity of the multigrid building blocks (Sec. 2, Alg. 1) and of the
+JFNK solve (Sec. 1, Sec. 3) against the oracle, through the C ABI.
+
+FD-driven components (power method, smoother, coarse GMRES, V-cycle) carry the
+FD round-off of each action (about eps_p / eps relative, ~1e-8 for FP64), so
+GPU and oracle agree to ~1e-6 relative, not to the last bit; transfers are
+exact linear maps and agree to round-off."""
+import numpy as np
+import pytest
+
+from gpu_common import dev, host, jf, rel, torch
+from oracle import adjoint, fem, jfnk, transfer
+from workloads import random_direction, random_state_field
+
+pytestmark = pytest.mark.gpu
+
+
+def _opts(**kw):
+    return jf().default_options(**kw)
+
+
+@pytest.mark.parametrize("d,n", [(2, 8), (2, 66), (3, 6), (3, 34)])
+@pytest.mark.parametrize("dt", ["f64", "f32"])
+def test_transfers_parity(d, n, dt):
+    kind = "bratu2d" if d == 2 else "nd3d"
+    p = jf().Problem(kind, n, 2, lam=1.0)
+    tdt = torch.float64 if dt == "f64" else torch.float32
+    tol = 1e-14 if dt == "f64" else 1e-6
+    xf = random_state_field(n, d, seed=3, kind="uniform")
+    xf[fem.boundary_mask(xf.shape)] = 0.0
+    xb = xf.copy()
+    xb[fem.boundary_mask(xb.shape)] = 0.7   # Dirichlet data for the projection
+    c = random_state_field(n // 2, d, seed=4, kind="uniform")
+    r = host(p.transfer("restrict", dev(xf, tdt)))
+    assert rel(r, transfer.restrict(xf)) <= tol
+    pr = host(p.transfer("project", dev(xb, tdt)))
+    assert rel(pr, transfer.project(xb)) <= tol
+    s0 = random_state_field(n, d, seed=5, kind="uniform")
+    out = dev(s0, tdt)
+    p.transfer("prolong_add", dev(c, tdt), out=out)
+    assert rel(host(out), s0 + transfer.prolong(c)) <= tol
+
+
+def _setup_pair(kind, n, levels, pc="f64", seed=0, lam=5.0, **kw):
+    """GPU problem after mg_setup at a seeded state, and the oracle hierarchy
+    after the same set-up."""
+    d = fem.dim_of(kind)
+    o = _opts(pc_dtype=jf().F32 if pc == "f32" else jf().F64,
+              eps_mode_pc=jf().EPS_FP32 if pc == "f32" else jf().EPS_PAPER, seed=seed, **kw)
+    p = jf().Problem(kind, n, levels, lam=lam, options=o)
+    u = random_state_field(n, d, seed=9, kind="mms" if kind == "nd3d" else "uniform",
+                           amplitude=0.1 if kind == "nd3d" else 0.5)
+    ud = dev(u)
+    p.mg_setup(ud, 0)
+    load = fem.mms_load(n) if kind == "nd3d" else None
+    lv = jfnk.build_hierarchy(kind, n, levels, lam=lam, load=load)
+    oo = jfnk.Options(nu_pre=o.nu_pre, nu_post=o.nu_post, cheb_degree=o.cheb_degree, power_iters=o.power_iters,
+                      eps_mode_pc="fp32" if pc == "f32" else "paper", seed=seed)
+    jfnk.setup_levels(lv, u, oo, 0)
+    return p, o, lv, oo, u
+
+
+@pytest.mark.parametrize("kind,n,levels", [("bratu2d", 64, 4), ("nd3d", 32, 4)])
+def test_setup_projection_operator_and_power_method(kind, n, levels):
+    p, o, lv, oo, u = _setup_pair(kind, n, levels)
+    for l in range(levels):
+        x = host(p.level_vector(l, "x"))
+        assert rel(x, lv[l].x) <= 1e-14
+        Ax = host(p.level_vector(l, "Ax"))
+        A_ora = fem.operator(kind, lv[l].x, 5.0)
+        assert rel(Ax, A_ora) <= 1e-12
+        info = p.level_info(l)
+        m = lv[l].mask
+        assert info["sum_abs_x"] == pytest.approx(np.abs(lv[l].x[m]).sum(), rel=1e-12)
+        if l >= 1:
+            # same SplitMix64 start vector, 10 FD power iterations on both sides
+            assert info["lambda_max"] == pytest.approx(lv[l].lam_max, rel=1e-6), l
+            pv = host(p.level_vector(l, "power"))
+            assert rel(pv, lv[l].power_v) <= 1e-5
+
+
+@pytest.mark.parametrize("kind,n,levels", [("bratu2d", 64, 4), ("nd3d", 32, 4)])
+@pytest.mark.parametrize("nu,zero", [(1, True), (3, True), (2, False)])
+def test_chebyshev_smoother_parity(kind, n, levels, nu, zero):
+    p, o, lv, oo, u = _setup_pair(kind, n, levels)
+    l = levels - 1
+    d = fem.dim_of(kind)
+    b = random_direction(n, d, seed=31) * 1e-3
+    s0 = np.zeros_like(b) if zero else random_direction(n, d, seed=32) * 1e-3
+    s = dev(s0)
+    p.smooth(dev(b), s, level=l, nu=nu, s_is_zero=zero)
+    lam = p.level_info(l)["lambda_max"]
+    so = jfnk.chebyshev(lv[l], s0.copy(), lv[l].x, lv[l].Fx, b, nu, o.cheb_degree, lam, o.cheb_lo, o.cheb_hi)
+    assert rel(host(s), so) <= 1e-6
+
+
+@pytest.mark.parametrize("kind,n,levels", [("bratu2d", 64, 4), ("nd3d", 32, 4)])
+def test_coarse_gmres_parity(kind, n, levels):
+    p, o, lv, oo, u = _setup_pair(kind, n, levels)
+    d = fem.dim_of(kind)
+    n0 = n >> (levels - 1)
+    b = random_direction(n0, d, seed=41)
+    s = host(p.coarse_solve(dev(b)))
+    lv0 = lv[0]
+    so, its, _ = jfnk.gmres(lambda v: jfnk.fd_jv(lv0, lv0.x, lv0.Fx, v), b, lv0.mask, 1e-12, lv0.n_unknowns)
+    assert rel(s, so) <= 1e-6
+
+
+@pytest.mark.parametrize("kind,n,levels", [("bratu2d", 64, 4), ("nd3d", 32, 4), ("nd3d", 16, 2)])
+def test_vcycle_parity(kind, n, levels):
+    """One V-cycle of Alg. 1 with the GPU's lambda_l given to the oracle."""
+    kw = dict(nu_pre=2, nu_post=2, cheb_degree=4) if kind == "nd3d" else {}
+    p, o, lv, oo, u = _setup_pair(kind, n, levels, **kw)
+    for l in range(1, levels):
+        lv[l].lam_max = p.level_info(l)["lambda_max"]
+    b = random_direction(n, fem.dim_of(kind), seed=51)
+    s = host(p.mg_vcycle(dev(b)))
+    so = jfnk.mg_vcycle(lv, levels - 1, b, oo)
+    assert rel(s, so) <= 1e-6
+
+
+@pytest.mark.parametrize("pc", ["f64", "f32"])
+def test_vcycle_fp32_parity_and_contraction(pc):
+    """The FP32 preconditioner agrees with the FP64 oracle to FP32 accuracy and
+    both contract the linearised error like a multigrid cycle."""
+    kind, n, levels = "bratu2d", 64, 4
+    p, o, lv, oo, u = _setup_pair(kind, n, levels, pc=pc)
+    for l in range(1, levels):
+        lv[l].lam_max = p.level_info(l)["lambda_max"]
+    b = random_direction(n, 2, seed=61)
+    bd = dev(b, torch.float64)
+    s = host(p.mg_vcycle(bd))
+    so = jfnk.mg_vcycle(lv, levels - 1, b, oo)
+    assert rel(s, so) <= (1e-6 if pc == "f64" else 2e-3)
+
+
+@pytest.mark.parametrize("pc", ["f64", "f32"])
+def test_solve_bratu_matches_discrete_solution(pc):
+    """Bratu lambda = 5 on 65x65 nodes, 4 levels, V(3,3) degree 3, FGMRES(30),
+    rtol 1e-10: the GPU solution equals the exact-Newton discrete solution."""
+    n = 64
+    o = _opts(rtol_newton=1e-11, pc_dtype=jf().F32 if pc == "f32" else jf().F64,
+              eps_mode_pc=jf().EPS_FP32 if pc == "f32" else jf().EPS_PAPER)
+    p = jf().Problem("bratu2d", n, 4, lam=5.0, options=o)
+    u = torch.zeros((n + 1, n + 1), dtype=torch.float64, device="cuda")
+    st = p.solve(u)
+    ud, _ = adjoint.newton_direct("bratu2d", np.zeros((n + 1, n + 1)), lam=5.0)
+    assert st["converged"]
+    assert rel(host(u), ud) <= 1e-8
+    assert st["newton_its"] <= 6
+
+
+@pytest.mark.parametrize("pc", ["f64", "f32"])
+def test_solve_nd_matches_discrete_solution(pc):
+    n = 32
+    o = _opts(rtol_newton=1e-11, nu_pre=2, nu_post=2, cheb_degree=4,
+              pc_dtype=jf().F32 if pc == "f32" else jf().F64,
+              eps_mode_pc=jf().EPS_FP32 if pc == "f32" else jf().EPS_PAPER)
+    p = jf().Problem("nd3d", n, 4, options=o)
+    u = torch.zeros((n + 1,) * 3, dtype=torch.float64, device="cuda")
+    st = p.solve(u)
+    ud, _ = adjoint.newton_direct("nd3d", np.zeros((n + 1,) * 3), load=fem.mms_load(n))
+    assert st["converged"]
+    assert rel(host(u), ud) <= 1e-8

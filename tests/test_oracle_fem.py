@@ -191,3 +191,11 @@ def test_vjp_matches_assembled_transpose_and_kappa_derivative():
         km = kap.copy(); km[e] -= 0.5
         dF = fem.residual("ndk3d", u, kappa=kp) - fem.residual("ndk3d", u, kappa=km)
         assert abs(np.sum(dF[m] * w[m]) - dk[e]) <= 1e-12 * (abs(dk[e]) + 1e-12)
+
+
+def test_mms_load_at_samples_matches_full():
+    n = 6
+    b = fem.mms_load(n)
+    rng = np.random.default_rng(3)
+    nodes = [tuple(rng.integers(0, n + 1, size=3)) for _ in range(25)]
+    assert np.allclose(fem.mms_load_at(n, nodes), [b[nd] for nd in nodes], rtol=1e-13, atol=1e-18)
