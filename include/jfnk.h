@@ -197,6 +197,34 @@ jfnk_status jfnk_level_info(jfnk_problem* p, int level, double* lambda_max, doub
  * which = 0: x_l, 1: A(x_l), 2: the power-method vector. */
 jfnk_status jfnk_level_vector(jfnk_problem* p, int level, int which, void* out, void* stream);
 
+/* ---- workspace-free FD Jacobian action ------------------------------------
+ * The paper has no counterpart to this entry point; it exists for callers that
+ * cannot call cudaMalloc (code that runs where device allocation is forbidden
+ * or would stall, or whose device memory is fully reserved by another
+ * allocator) and therefore cannot provide the workspace jfnk_jvp needs.
+ *
+ * Computes the same Jv = (F(u + eps v) - F(u)) / eps as jfnk_jvp on the finest
+ * level of a one-level problem described inline: kind, n_elem, lambda (Bratu),
+ * kappa (NDK3D, per element, in dtype) and load (ND3D, nullable, in dtype: the
+ * load vector included in Fu; NDK3D always includes its unit load).  eps > 0 is
+ * used as given, eps <= 0 selects eps_mode.
+ *
+ * It allocates nothing: its scratch (reduction partials for up to 2048 CTAs,
+ * completion counters, the FD step; about 16 KB) is a file-scope __device__
+ * array that every GPU which loads libjfnk.so holds until the process exits.
+ * Sizes: 2 <= n_elem <= JFNK_NOALLOC_MAX_N3D (3D) or JFNK_NOALLOC_MAX_N2D (2D);
+ * larger grids return JFNK_ERR_INVALID_ARG.  The first call on a device looks up
+ * the scratch's device address (with that device current); make that first call
+ * before any stream capture.  Every call clears the completion counters it needs
+ * on `stream` and otherwise reuses the previous call's scratch contents, so calls
+ * that overlap on the GPU (other streams, other threads) race on the scratch:
+ * serialise them. */
+#define JFNK_NOALLOC_MAX_N3D 512
+#define JFNK_NOALLOC_MAX_N2D 16384
+jfnk_status jfnk_jvp_noalloc(int kind, int n_elem, double lambda, const void* kappa, const void* load, int dtype,
+                             const void* u, const void* Fu, const void* v, void* Jv, double eps, int eps_mode,
+                             void* stream);
+
 /* Limits of the single-CTA coarse solver and of FGMRES. */
 #define JFNK_COARSE_MAX_NODES 1024
 #define JFNK_COARSE_MAX_IT 512

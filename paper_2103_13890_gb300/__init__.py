@@ -210,6 +210,19 @@ class Problem:
             pass
 
 
+def jvp_noalloc(kind, u, Fu, v, lam=0.0, kappa=None, load=None, eps=0.0, eps_mode=EPS_PAPER, out=None):
+    """FD Jacobian action without a problem object or workspace (jfnk_jvp_noalloc),
+    for callers that cannot allocate device memory; kappa and load must have u's
+    dtype.  Calls that overlap on the GPU share the library's fixed scratch."""
+    n = u.shape[0] - 1
+    out = torch.empty_like(u) if out is None else out
+    kp = _ptr(kappa) if kappa is not None else None
+    lp = _ptr(load) if load is not None else None
+    _check(lib().jfnk_jvp_noalloc(KINDS[kind], n, float(lam), kp, lp, _dtype_code(u), _ptr(u), _ptr(Fu), _ptr(v),
+                                  _ptr(out), float(eps), int(eps_mode), _stream()))
+    return out
+
+
 def kernel_launches(reset=False):
     return lib().jfnk_kernel_launches(1 if reset else 0)
 

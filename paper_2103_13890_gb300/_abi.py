@@ -63,6 +63,7 @@ SIGNATURES = [
     ("jfnk_level_vector", _i, [_vp, _i, _i, _vp, _vp]),
     ("jfnk_last_error", ctypes.c_char_p, []),
     ("jfnk_kernel_launches", ctypes.c_longlong, [_i]),
+    ("jfnk_jvp_noalloc", _i, [_i, _i, _d, _vp, _vp, _i, _vp, _vp, _vp, _vp, _d, _i, _vp]),
     ("jfnk_profile_enable", None, [_i]),
     ("jfnk_profile_read", _i, [_i, ctypes.c_char_p, _i, ctypes.POINTER(ctypes.c_longlong),
                                ctypes.POINTER(_d), ctypes.POINTER(_d)]),

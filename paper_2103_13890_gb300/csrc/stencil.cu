@@ -399,6 +399,14 @@ jfnk_status launch_stencil(Prob prob, Mode mode, const StencilArgs<T>& a, cudaSt
     return s;
 }
 
+// Launch without the optional event profiler (which creates CUDA events).
+template <typename T>
+jfnk_status launch_stencil_direct(Prob prob, Mode mode, const StencilArgs<T>& a, cudaStream_t st) {
+    return launch_stencil_impl<T>(prob, mode, a, st);
+}
+template jfnk_status launch_stencil_direct<double>(Prob, Mode, const StencilArgs<double>&, cudaStream_t);
+template jfnk_status launch_stencil_direct<float>(Prob, Mode, const StencilArgs<float>&, cudaStream_t);
+
 template jfnk_status launch_stencil<double>(Prob, Mode, const StencilArgs<double>&, cudaStream_t);
 template jfnk_status launch_stencil<float>(Prob, Mode, const StencilArgs<float>&, cudaStream_t);
 
