@@ -1,0 +1,97 @@
+"""Micro-benchmark of single hot-path operations through the C ABI.
+
+    python -m paper_2103_13890_gb300.kernelbench --kind nd3d --n 160 --op smooth --dtype f64
+
+op: residual | jvp | smooth (one Chebyshev application = start + fused steps)
+    | vcycle.  Prints one JSON line with the mean time per call (CUDA events on
+the current stream, after warm-up) and, for the element kernels, the achieved
+FP64/FP32 operation rate and HBM bandwidth of the algorithmic traffic.
+"""
+import argparse
+import json
+
+import torch
+
+import paper_2103_13890_gb300 as jf
+
+OPS_PER_ELEMENT = {"nd3d": 164, "ndk3d": 172, "bratu2d": 42}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--kind", default="nd3d", choices=list(OPS_PER_ELEMENT))
+    ap.add_argument("--n", type=int, default=128)
+    ap.add_argument("--levels", type=int, default=0, help="0: coarsest level with 4 elements")
+    ap.add_argument("--op", default="residual", choices=["residual", "jvp", "smooth", "vcycle"])
+    ap.add_argument("--dtype", default="f64", choices=["f64", "f32"])
+    ap.add_argument("--reps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    a = ap.parse_args()
+    d = 2 if a.kind == "bratu2d" else 3
+    n = a.n
+    levels = a.levels
+    if levels == 0:
+        levels = 1
+        while (n >> levels) >= 4 and ((n >> levels) << levels) == n:
+            levels += 1
+    dt = torch.float64 if a.dtype == "f64" else torch.float32
+    o = jf.default_options(pc_dtype=jf.F64 if a.dtype == "f64" else jf.F32,
+                           eps_mode_pc=jf.EPS_PAPER if a.dtype == "f64" else jf.EPS_FP32,
+                           nu_pre=2, nu_post=2, cheb_degree=4)
+    kappa = None
+    if a.kind == "ndk3d":
+        g = torch.Generator().manual_seed(0)
+        kappa = torch.exp(torch.randn((n,) * 3, generator=g, dtype=torch.float64))
+    p = jf.Problem(a.kind, n, levels, lam=5.0, kappa=kappa, options=o)
+    shape = (n + 1,) * d
+    g = torch.Generator(device="cuda").manual_seed(1)
+    u = (torch.rand(shape, generator=g, device="cuda", dtype=torch.float64) - 0.5) * 0.2
+    bnd = torch.ones(shape, dtype=torch.bool, device="cuda")
+    inner = tuple(slice(1, -1) for _ in range(d))
+    bnd[inner] = False
+    u[bnd] = 0.0
+    v = torch.randn(shape, generator=g, device="cuda", dtype=torch.float64)
+    v[bnd] = 0.0
+    if a.op in ("smooth", "vcycle"):
+        p.mg_setup(u, 0)
+    uT, vT = u.to(dt), v.to(dt)
+    F = p.residual(uT)
+    out = torch.empty_like(uT)
+    s = torch.zeros_like(uT)
+
+    def call():
+        if a.op == "residual":
+            p.residual(uT, out=out)
+        elif a.op == "jvp":
+            p.jvp(uT, F, vT, out=out, eps=1e-7)
+        elif a.op == "smooth":
+            s.zero_()
+            p.smooth(vT, s, level=levels - 1, nu=1, s_is_zero=True)
+        else:
+            p.mg_vcycle(v, out=out.double() if a.dtype == "f32" else out)
+
+    for _ in range(a.warmup):
+        call()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(a.reps):
+        call()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / a.reps
+    elems = n ** d
+    w = 8 if a.dtype == "f64" else 4
+    nodes = (n + 1) ** d
+    stencils = {"residual": 1, "jvp": 1, "smooth": o.cheb_degree - 1}.get(a.op)
+    words = {"residual": 2 + (1 if a.kind == "nd3d" else 0), "jvp": 4}.get(a.op)
+    line = {"kind": a.kind, "n": n, "levels": levels, "op": a.op, "dtype": a.dtype, "ms": ms}
+    if stencils:
+        line["ops_per_s"] = OPS_PER_ELEMENT[a.kind] * elems * stencils / (ms * 1e-3)
+    if words:
+        line["gbs"] = words * w * nodes / (ms * 1e-3) / 1e9
+    print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    main()
