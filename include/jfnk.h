@@ -98,6 +98,7 @@ typedef struct {
     int line_search;         /* 1: cubic backtracking (Sec. 3), 0: full steps */
     int ls_max;              /* backtracking steps */
     uint64_t seed;           /* power-method start vector (SplitMix64 stream) */
+    int use_graph;           /* 1: capture the V-cycle once in a CUDA graph and replay it */
 } jfnk_options;
 
 #define JFNK_MAX_LEVELS 16
@@ -196,6 +197,32 @@ jfnk_status jfnk_level_info(jfnk_problem* p, int level, double* lambda_max, doub
 /* Copy a level vector set by jfnk_mg_setup into out (opts->pc_dtype):
  * which = 0: x_l, 1: A(x_l), 2: the power-method vector. */
 jfnk_status jfnk_level_vector(jfnk_problem* p, int level, int which, void* out, void* stream);
+
+/* ---- adjoint: vector-Jacobian products and the adjoint solve --------------
+ * For the 3D diffusion problems F_i = sum_e kappa_e int_e (1+u^2) grad u.grad phi_i - b_i
+ * (kappa = 1 for ND3D) the transposed Jacobian acts as
+ *   (J^T w)_j = sum_e kappa_e int_e (1+u^2) grad w.grad phi_j + 2u (grad u.grad w) phi_j
+ * and (dF/dkappa_e)^T w = int_e (1+u^2) grad u.grad w (boundary entries of w ignored).
+ * The paper has no adjoint; these follow from differentiating its F. */
+
+/* JTw = J(u)^T w on a level (dtype vectors, full node grids); dFdkappa_w
+ * (nullable, NDK3D only, n_l^3 per-element values) = (dF/dkappa)^T w. */
+jfnk_status jfnk_vjp(jfnk_problem* p, int level, int dtype, const void* u, const void* w, void* JTw,
+                     void* dFdkappa_w, void* stream);
+
+/* Replace the coefficient field of an NDK3D problem (device FP64, n_elem^3,
+ * copied) and rebuild the coarse-level coefficients (arithmetic means). */
+jfnk_status jfnk_set_kappa(jfnk_problem* p, const double* kappa, void* stream);
+
+/* Adjoint solve at a solution u (FP64): J(u)^T lambda = g by FGMRES(m) with
+ * the V-cycle of Algorithm 1 run on J^T (Chebyshev smoothing, restriction,
+ * coarse GMRES with the exact vector-Jacobian product; preconditioner in
+ * opts->pc_dtype), to ||g - J^T lambda|| <= rtol ||g||.  g's boundary entries
+ * are ignored.  If grad_kappa is given (NDK3D): grad_kappa = -(dF/dkappa)^T lambda,
+ * the gradient of L(u(kappa)) with dL/du = g (implicit-function theorem).
+ * Synchronises the stream; stats (nullable) gets iteration counts and GE. */
+jfnk_status jfnk_adjoint_solve(jfnk_problem* p, const jfnk_options* opts, const double* u, const double* g,
+                               double* lambda, double* grad_kappa, double rtol, jfnk_stats* stats, void* stream);
 
 /* ---- workspace-free FD Jacobian action ------------------------------------
  * The paper has no counterpart to this entry point; it exists for callers that

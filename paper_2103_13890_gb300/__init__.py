@@ -187,6 +187,35 @@ class Problem:
         _check(lib().jfnk_level_vector(self._h, level, code, _ptr(out), _stream()))
         return out
 
+    def vjp(self, u, w, level=None, dkappa=False, out=None):
+        """J(u)^T w (and (dF/dkappa)^T w per element when dkappa=True)."""
+        lv = self._lv(level)
+        out = torch.empty_like(u) if out is None else out
+        dk = None
+        if dkappa:
+            m = self.n >> (self.levels - 1 - lv)
+            dk = torch.empty((m,) * 3, dtype=u.dtype, device=u.device)
+        _check(lib().jfnk_vjp(self._h, lv, _dtype_code(u), _ptr(u), _ptr(w), _ptr(out),
+                              _ptr(dk) if dk is not None else None, _stream()))
+        return (out, dk) if dkappa else out
+
+    def set_kappa(self, kappa):
+        kappa = kappa.to(self.device, torch.float64).contiguous()
+        self._keep.append(kappa)
+        self._keep = self._keep[-2:]
+        _check(lib().jfnk_set_kappa(self._h, _ptr(kappa), _stream()))
+
+    def adjoint_solve(self, u, g, rtol=1e-10, grad=True, options=None):
+        """lambda with J(u)^T lambda = g, and grad_kappa = -(dF/dkappa)^T lambda."""
+        o = options or self.options
+        lam = torch.empty_like(u)
+        gk = torch.empty((self.n,) * 3, dtype=torch.float64, device=u.device) if grad else None
+        st = _abi.Stats()
+        _check(lib().jfnk_adjoint_solve(self._h, ctypes.byref(o), _ptr(u), _ptr(g.contiguous()), _ptr(lam),
+                                        _ptr(gk) if gk is not None else None, float(rtol), ctypes.byref(st),
+                                        _stream()))
+        return lam, gk, {"linear_its": st.linear_its, "ge": st.ge, "solve_ms": st.solve_ms}
+
     def solve(self, u, options=None, check=True):
         """Inexact JFNK solve in place on u (FP64, full node grid).  Returns stats."""
         o = options or self.options

@@ -31,7 +31,7 @@ class Options(ctypes.Structure):
                 ("eta_max", ctypes.c_double), ("coarse_tol", ctypes.c_double), ("coarse_tol_mode", ctypes.c_int),
                 ("coarse_maxit", ctypes.c_int), ("pc_dtype", ctypes.c_int), ("eps_mode_pc", ctypes.c_int),
                 ("max_newton", ctypes.c_int), ("line_search", ctypes.c_int), ("ls_max", ctypes.c_int),
-                ("seed", ctypes.c_uint64)]
+                ("seed", ctypes.c_uint64), ("use_graph", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -64,6 +64,9 @@ SIGNATURES = [
     ("jfnk_last_error", ctypes.c_char_p, []),
     ("jfnk_kernel_launches", ctypes.c_longlong, [_i]),
     ("jfnk_jvp_noalloc", _i, [_i, _i, _d, _vp, _vp, _i, _vp, _vp, _vp, _vp, _d, _i, _vp]),
+    ("jfnk_vjp", _i, [_vp, _i, _i, _vp, _vp, _vp, _vp, _vp]),
+    ("jfnk_set_kappa", _i, [_vp, _vp, _vp]),
+    ("jfnk_adjoint_solve", _i, [_vp, ctypes.POINTER(Options), _vp, _vp, _vp, _vp, _d, ctypes.POINTER(Stats), _vp]),
     ("jfnk_profile_enable", None, [_i]),
     ("jfnk_profile_read", _i, [_i, ctypes.c_char_p, _i, ctypes.POINTER(ctypes.c_longlong),
                                ctypes.POINTER(_d), ctypes.POINTER(_d)]),

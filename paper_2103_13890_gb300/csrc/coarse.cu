@@ -83,6 +83,49 @@ __device__ void coarse_apply_A(const Grid& g, const T* w, T* elemC, T* out, cons
     __syncthreads();
 }
 
+// J(x)^T v on the coarse grid (3D diffusion problems), full grid out (boundary untouched)
+template <typename T, Prob P>
+__device__ void coarse_apply_vjp(const Grid& g, const T* x, const T* v, T* elemC, T* out, const T* kappa,
+                                 T node_scale) {
+    const int n = g.n;
+    const int tid = threadIdx.x;
+    const int ne = n * n * n;
+    for (int e = tid; e < ne; e += blockDim.x) {
+        const int ex = e % n, ey = (e / n) % n, ez = e / (n * n);
+        const long long b = (long long)ez * g.sz + (long long)ey * g.sy + ex;
+        const long long o[8] = {0, 1, g.sy, g.sy + 1, g.sz, g.sz + 1, g.sz + g.sy, g.sz + g.sy + 1};
+        T ue[8], ve[8];
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            ue[c] = x[b + o[c]];
+            ve[c] = v[b + o[c]];
+        }
+        T r[8], dk;
+        elem_vjp3<T>(ue, ve, P == Prob::NDK3 ? kappa[e] : T(1), r, dk);
+#pragma unroll
+        for (int c = 0; c < 8; ++c) elemC[e * 8 + c] = r[c];
+    }
+    __syncthreads();
+    for (long long i = tid; i < g.size; i += blockDim.x) {
+        const int xx = (int)(i % g.sy);
+        const int yy = (int)((i / g.sy) % g.ny);
+        const int zz = (int)(i / g.sz);
+        T acc = T(0);
+#pragma unroll
+        for (int c = 0; c < 2; ++c)
+#pragma unroll
+            for (int bb = 0; bb < 2; ++bb)
+#pragma unroll
+                for (int a = 0; a < 2; ++a) {
+                    const int ex = xx - 1 + a, ey = yy - 1 + bb, ez = zz - 1 + c;
+                    if (ex >= 0 && ex < n && ey >= 0 && ey < n && ez >= 0 && ez < n)
+                        acc += elemC[((ez * n + ey) * n + ex) * 8 + (1 - a) + 2 * (1 - bb) + 4 * (1 - c)];
+                }
+        out[i] = acc * node_scale;
+    }
+    __syncthreads();
+}
+
 __device__ __forceinline__ bool coarse_inner(const Grid& g, long long i) {
     const int x = (int)(i % g.sy);
     const int y = (int)((i / g.sy) % g.ny);
@@ -94,7 +137,7 @@ __device__ __forceinline__ bool coarse_inner(const Grid& g, long long i) {
     return in;
 }
 
-template <typename T, Prob P>
+template <typename T, Prob P, bool ADJ>
 __global__ void __launch_bounds__(kCoarseThreads) coarse_gmres_kernel(CoarseArgs<T> a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const Grid g = a.g;
@@ -155,11 +198,19 @@ __global__ void __launch_bounds__(kCoarseThreads) coarse_gmres_kernel(CoarseArgs
             s_scalar[2] = e > 0.0 ? 1.0 / e : 0.0;
         }
         __syncthreads();
-        const T eps = (T)s_scalar[1], inv_eps = (T)s_scalar[2];
-        for (int i = tid; i < N; i += blockDim.x) xw[i] = a.x[i] + (coarse_inner(g, i) ? eps * vj[i] : T(0));
-        __syncthreads();
-        coarse_apply_A<T, P>(g, xw, elemC, Aw, a.kappa, a.lh, a.node_scale);
-        for (int i = tid; i < N; i += blockDim.x) wv[i] = coarse_inner(g, i) ? (Aw[i] - a.Ax[i]) * inv_eps : T(0);
+        if (ADJ) {
+            // adjoint operator: J(x_0)^T v_j, exact, element by element
+            for (int i = tid; i < N; i += blockDim.x) xw[i] = coarse_inner(g, i) ? vj[i] : T(0);
+            __syncthreads();
+            coarse_apply_vjp<T, P>(g, a.x, xw, elemC, Aw, a.kappa, a.node_scale);
+            for (int i = tid; i < N; i += blockDim.x) wv[i] = coarse_inner(g, i) ? Aw[i] : T(0);
+        } else {
+            const T eps = (T)s_scalar[1], inv_eps = (T)s_scalar[2];
+            for (int i = tid; i < N; i += blockDim.x) xw[i] = a.x[i] + (coarse_inner(g, i) ? eps * vj[i] : T(0));
+            __syncthreads();
+            coarse_apply_A<T, P>(g, xw, elemC, Aw, a.kappa, a.lh, a.node_scale);
+            for (int i = tid; i < N; i += blockDim.x) wv[i] = coarse_inner(g, i) ? (Aw[i] - a.Ax[i]) * inv_eps : T(0);
+        }
         __syncthreads();
         // classical Gram-Schmidt, twice; h accumulated in hcol
         for (int i = tid; i <= j; i += blockDim.x) hcol[i] = 0.0;
@@ -259,23 +310,28 @@ jfnk_status launch_coarse(Prob prob, const CoarseArgs<T>& a, cudaStream_t st) {
         set_error("coarse solver shared memory %zu too large", smem);
         return JFNK_ERR_INVALID_ARG;
     }
+    if (a.adjoint && prob == Prob::BRATU2) {
+        set_error("the adjoint coarse solve is implemented for the 3D diffusion problems");
+        return JFNK_ERR_NOT_IMPLEMENTED;
+    }
+#define JFNK_COARSE_LAUNCH(PP, ADJ)                                                                  \
+    do {                                                                                             \
+        JFNK_CUDA_TRY(cudaFuncSetAttribute(coarse_gmres_kernel<T, PP, ADJ>,                           \
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)); \
+        coarse_gmres_kernel<T, PP, ADJ><<<1, kCoarseThreads, smem, st>>>(a);                          \
+    } while (0)
     switch (prob) {
-        case Prob::BRATU2:
-            JFNK_CUDA_TRY(cudaFuncSetAttribute(coarse_gmres_kernel<T, Prob::BRATU2>,
-                                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-            coarse_gmres_kernel<T, Prob::BRATU2><<<1, kCoarseThreads, smem, st>>>(a);
-            break;
+        case Prob::BRATU2: JFNK_COARSE_LAUNCH(Prob::BRATU2, false); break;
         case Prob::ND3:
-            JFNK_CUDA_TRY(cudaFuncSetAttribute(coarse_gmres_kernel<T, Prob::ND3>,
-                                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-            coarse_gmres_kernel<T, Prob::ND3><<<1, kCoarseThreads, smem, st>>>(a);
+            if (a.adjoint) JFNK_COARSE_LAUNCH(Prob::ND3, true);
+            else JFNK_COARSE_LAUNCH(Prob::ND3, false);
             break;
         case Prob::NDK3:
-            JFNK_CUDA_TRY(cudaFuncSetAttribute(coarse_gmres_kernel<T, Prob::NDK3>,
-                                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-            coarse_gmres_kernel<T, Prob::NDK3><<<1, kCoarseThreads, smem, st>>>(a);
+            if (a.adjoint) JFNK_COARSE_LAUNCH(Prob::NDK3, true);
+            else JFNK_COARSE_LAUNCH(Prob::NDK3, false);
             break;
     }
+#undef JFNK_COARSE_LAUNCH
     JFNK_LAUNCH_CHECK();
     return JFNK_OK;
 }

@@ -23,6 +23,7 @@ struct CoarseArgs {
     T* V;                  // (maxit + 1) * g.size scratch
     double* H;             // (maxit + 1) * maxit scratch
     long long* iters;      // device accumulator of GMRES iterations (GE count), nullable
+    int adjoint;           // 1: solve with J(x_0)^T (exact VJP) instead of the FD action
 };
 
 template <typename T>

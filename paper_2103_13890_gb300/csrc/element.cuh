@@ -138,6 +138,117 @@ __host__ __device__ __forceinline__ void elem_nd3(const T u[8], T kap, T r[8]) {
 }
 
 // ---------------------------------------------------------------------------
+// 3D vector-Jacobian product of the coefficient problem (adjoint).
+//   F_i = sum_e kap_e int_e (1+u^2) grad u . grad phi_i - int phi_i, so for a
+//   (boundary-masked) w:
+//   (J^T w)_b  = kap int_e (1+u^2) grad w . grad phi_b + 2 u (grad u . grad w) phi_b
+//   (dF/dkap_e)^T w = int_e (1+u^2) grad u . grad w
+// u[8], w[8] nodal values (index a + 2b + 4c).  r[8] receives (J^T w)_b / (3h/16),
+// dk receives (dF/dkap_e)^T w / (3h/2).  The first term has the residual's
+// structure with grad w in the flux; the second is a mass-like term whose test
+// side is the transpose of the 3D Gauss-point interpolation.
+// ---------------------------------------------------------------------------
+template <typename T>
+__host__ __device__ __forceinline__ void modal_scaled3(const T u[8], T S[8]) {
+    // S[p + 2q + 4r] = M'_pqr A^(p+q+r) / 8 with M' = T' (x) T' (x) T' u
+    const T A1 = T(0.57735026918962576451);
+    const T A2 = T(0.33333333333333333333);
+    const T A3 = T(0.19245008972987525484);
+    T p0 = u[0] + u[1], q0 = u[1] - u[0];
+    T p1 = u[2] + u[3], q1 = u[3] - u[2];
+    T p2 = u[4] + u[5], q2 = u[5] - u[4];
+    T p3 = u[6] + u[7], q3 = u[7] - u[6];
+    T a00 = p0 + p1, a01 = p1 - p0, b00 = p2 + p3, b01 = p3 - p2;
+    T a10 = q0 + q1, a11 = q1 - q0, b10 = q2 + q3, b11 = q3 - q2;
+    S[0] = (a00 + b00) * T(0.125);
+    S[4] = (b00 - a00) * (A1 * T(0.125));
+    S[2] = (a01 + b01) * (A1 * T(0.125));
+    S[6] = (b01 - a01) * (A2 * T(0.125));
+    S[1] = (a10 + b10) * (A1 * T(0.125));
+    S[5] = (b10 - a10) * (A2 * T(0.125));
+    S[3] = (a11 + b11) * (A2 * T(0.125));
+    S[7] = (b11 - a11) * (A3 * T(0.125));
+}
+
+template <typename T>
+__host__ __device__ __forceinline__ void elem_vjp3(const T u[8], const T w[8], T kap, T r[8], T& dk) {
+    const T A1 = T(0.57735026918962576451);
+    const T A2 = T(0.33333333333333333333);
+    const T A3 = T(0.19245008972987525484);
+    T Su[8], Sw[8];
+    modal_scaled3(u, Su);
+    modal_scaled3(w, Sw);
+    T P0[2][2], GXu[2][2], GYu[2][2], GZu[2][2], GXw[2][2], GYw[2][2], GZw[2][2];
+    h2_fwd(Su[0], Su[2], Su[4], Su[6], P0);   // [sy][sz]
+    h2_fwd(Su[1], Su[3], Su[5], Su[7], GXu);  // [sy][sz]
+    h2_fwd(Su[2], Su[3], Su[6], Su[7], GYu);  // [sx][sz]
+    h2_fwd(Su[4], Su[5], Su[6], Su[7], GZu);  // [sx][sy]
+    h2_fwd(Sw[1], Sw[3], Sw[5], Sw[7], GXw);
+    h2_fwd(Sw[2], Sw[3], Sw[6], Sw[7], GYw);
+    h2_fwd(Sw[4], Sw[5], Sw[6], Sw[7], GZw);
+    T c[2][2][2], src[2][2][2];
+    T dks = T(0);
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 2; ++j)
+#pragma unroll
+            for (int k = 0; k < 2; ++k) {
+                const T uq = i ? P0[j][k] + GXu[j][k] : P0[j][k] - GXu[j][k];
+                const T g = uq * uq + T(1);
+                const T dot = GXu[j][k] * GXw[j][k] + GYu[i][k] * GYw[i][k] + GZu[i][j] * GZw[i][j];
+                c[i][j][k] = kap * g;
+                src[i][j][k] = uq * dot;
+                dks += g * dot;
+            }
+    dk = dks;
+    T FX[2][2], FY[2][2], FZ[2][2];
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            FX[i][j] = GXw[i][j] * (c[1][i][j] + c[0][i][j]);
+            FY[i][j] = GYw[i][j] * (c[i][1][j] + c[i][0][j]);
+            FZ[i][j] = GZw[i][j] * (c[i][j][1] + c[i][j][0]);
+        }
+    T X00, X10, X01, X11, Y00, Y10, Y01, Y11, Z00, Z10, Z01, Z11;
+    h2_adj(FX, X00, X10, X01, X11);
+    h2_adj(FY, Y00, Y10, Y01, Y11);
+    h2_adj(FZ, Z00, Z10, Z01, Z11);
+    // E_pqr = sum over the 8 points of s_x^p s_y^q s_z^r src
+    T Ez0[2][2], Ez1[2][2];  // [sx][sy] sums / differences over sz
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            Ez0[i][j] = src[i][j][1] + src[i][j][0];
+            Ez1[i][j] = src[i][j][1] - src[i][j][0];
+        }
+    T E000, E100, E010, E110, E001, E101, E011, E111;
+    h2_adj(Ez0, E000, E100, E010, E110);
+    h2_adj(Ez1, E001, E101, E011, E111);
+    const T k2 = kap + kap;
+    const T R000 = k2 * E000;
+    const T R100 = (X00 + k2 * E100) * A1, R010 = (Y00 + k2 * E010) * A1, R001 = (Z00 + k2 * E001) * A1;
+    const T R110 = (X10 + Y10 + k2 * E110) * A2;
+    const T R101 = (X01 + Z10 + k2 * E101) * A2;
+    const T R011 = (Y01 + Z01 + k2 * E011) * A2;
+    const T R111 = (X11 + Y11 + Z11 + k2 * E111) * A3;
+    T e00_0 = R000 - R001, e00_1 = R000 + R001;
+    T e01_0 = R010 - R011, e01_1 = R010 + R011;
+    T e10_0 = R100 - R101, e10_1 = R100 + R101;
+    T e11_0 = R110 - R111, e11_1 = R110 + R111;
+    T f0_00 = e00_0 - e01_0, f0_10 = e00_0 + e01_0;
+    T f0_01 = e00_1 - e01_1, f0_11 = e00_1 + e01_1;
+    T f1_00 = e10_0 - e11_0, f1_10 = e10_0 + e11_0;
+    T f1_01 = e10_1 - e11_1, f1_11 = e10_1 + e11_1;
+    r[0] = f0_00 - f1_00; r[1] = f0_00 + f1_00;
+    r[2] = f0_10 - f1_10; r[3] = f0_10 + f1_10;
+    r[4] = f0_01 - f1_01; r[5] = f0_01 + f1_01;
+    r[6] = f0_11 - f1_11; r[7] = f0_11 + f1_11;
+}
+
+// ---------------------------------------------------------------------------
 // 2D Bratu element (Sec. 3).
 //   u[4]: nodal values, index a + 2b
 //   lh:   lambda h^2 / 16

@@ -28,6 +28,9 @@
 #include "stencil.cuh"
 #include "transfer.cuh"
 #include "vector.cuh"
+#include "profile.cuh"
+#include "stencil_v2.cuh"
+#include <algorithm>
 
 namespace jfnk {
 
@@ -77,6 +80,7 @@ struct jfnk_problem {
     size_t ws_bytes = 0;
     bool bound = false;
     bool has_solver = false;
+    bool adj = false;  // preconditioner and outer operator use J^T (adjoint solve)
     int pc = JFNK_F64;
     int m = 0;
     int coarse_maxit = 0;
@@ -94,6 +98,14 @@ struct jfnk_problem {
     void* coarseV;
     double* coarseH;
     double* mms_tab;
+    char* face = nullptr;  // face buffer of the halo-free 3D kernel
+    size_t face_bytes = 0;
+    // captured V-cycle (Lf.b -> Lf.s) and the options it was captured for
+    cudaGraphExec_t vgraph = nullptr;
+    cudaStream_t cap_stream = nullptr;
+    long long vgraph_key[12] = {0};
+    long long vgraph_nF[JFNK_MAX_LEVELS] = {0};
+    long long vgraph_launches = 0;
     // host counters
     long long nF[JFNK_MAX_LEVELS];
 };
@@ -151,6 +163,10 @@ static size_t plan(P& p, char* base, const jfnk_options* o) {
     }
     const Grid& gf = p.lv[p.L].g;
     const size_t N = (size_t)gf.size;
+    long long face = 0;
+    for (int l = 0; l <= p.L; ++l) face = std::max(face, v2_face_count(p.lv[l].g));
+    p.face_bytes = (size_t)face * sizeof(double);
+    p.face = face > 0 ? pl.take<char>(p.face_bytes) : nullptr;
     p.F64 = pl.take<double>(N);
     p.Au64 = pl.take<double>(N);
     p.tmp64 = pl.take<double>(N);
@@ -236,7 +252,17 @@ static StencilArgs<T> base_args(P& p, int l) {
     a.counter = &p.red->counter[1];
     a.status = p.status;
     a.red = RedOut::NONE;
+    a.face = reinterpret_cast<T*>(p.face);
+    a.face_cap = (long long)(p.face_bytes / sizeof(T));
     return a;
+}
+
+// Operator of the multigrid cycle: the FD action of F (forward) or the exact
+// vector-Jacobian product J^T v (adjoint solve).
+template <typename T>
+static jfnk_status launch_op(P& p, Mode m, const StencilArgs<T>& a, cudaStream_t st) {
+    if (p.adj) return launch_vjp<T>(prob_of(p), m, a, st);
+    return launch_stencil<T>(prob_of(p), m, a, st);
 }
 
 template <typename T>
@@ -272,7 +298,7 @@ static jfnk_status smooth(P& p, const jfnk_options& o, int l, const T* b, T* s, 
             a.red = RedOut::EPS;
             a.red_eps = L.eps_d;
             a.epsp = ep;
-            JFNK_TRY(launch_stencil<T>(prob_of(p), Mode::CHEB0, a, st));
+            JFNK_TRY(launch_op<T>(p, Mode::CHEB0, a, st));
             p.nF[l]++;
         }
         if (k == 1) {
@@ -295,10 +321,10 @@ static jfnk_status smooth(P& p, const jfnk_options& o, int l, const T* b, T* s, 
             a.epsp = ep;
             if (i < k - 2) {
                 a.red_eps = L.eps_d;
-                JFNK_TRY(launch_stencil<T>(prob_of(p), Mode::CHEB, a, st));
+                JFNK_TRY(launch_op<T>(p, Mode::CHEB, a, st));
             } else {
                 a.red_eps = L.eps_s;
-                JFNK_TRY(launch_stencil<T>(prob_of(p), Mode::CHEBLAST, a, st));
+                JFNK_TRY(launch_op<T>(p, Mode::CHEBLAST, a, st));
             }
             p.nF[l]++;
             T* tmp = dc;
@@ -331,6 +357,7 @@ static jfnk_status coarse_solve(P& p, const jfnk_options& o, const T* b, T* s, c
     a.V = as<T>(p.coarseV);
     a.H = p.coarseH;
     a.iters = p.coarse_iters;
+    a.adjoint = p.adj ? 1 : 0;
     return launch_coarse<T>(prob_of(p), a, st);
 }
 
@@ -351,7 +378,7 @@ static jfnk_status vcycle(P& p, const jfnk_options& o, int l, T* b, T* s, cudaSt
         a.Au = as<T>(L.Ax);
         a.rhs = b;
         a.out = as<T>(L.t);
-        JFNK_TRY(launch_stencil<T>(prob_of(p), Mode::BMJ, a, st));
+        JFNK_TRY(launch_op<T>(p, Mode::BMJ, a, st));
         p.nF[l]++;
     }
     JFNK_TRY(restrict_to<T>(L.g, C.g, as<T>(L.t), as<T>(C.b), false, st));
@@ -361,6 +388,49 @@ static jfnk_status vcycle(P& p, const jfnk_options& o, int l, T* b, T* s, cudaSt
     JFNK_TRY(prolong_add<T>(C.g, L.g, as<T>(C.s), s, st));
     JFNK_TRY(norm_to_eps<T>(L.g, s, eps_params(p, l, o.eps_mode_pc), L.eps_s, nullptr, p.red, st));
     JFNK_TRY(smooth<T>(p, o, l, b, s, o.nu_post, false, st));
+    return JFNK_OK;
+}
+
+// One V-cycle Lf.b -> Lf.s replayed from a CUDA graph.  Every launch of the
+// cycle reads its scalars (FD steps, Chebyshev coefficients, lambda_l) from
+// device memory, so the captured sequence stays valid across Newton steps; it
+// is recaptured when the options that shape it change.
+template <typename T>
+static jfnk_status vcycle_graph(P& p, const jfnk_options& o, cudaStream_t st) {
+    long long key[12] = {o.nu_pre, o.nu_post, o.cheb_degree, o.pc_dtype, o.eps_mode_pc, p.coarse_maxit, 0,
+                         o.coarse_tol_mode, p.adj ? 1 : 0, (long long)sizeof(T), 1, 0};
+    memcpy(&key[6], &o.coarse_tol, sizeof(double));
+    if (p.vgraph && memcmp(key, p.vgraph_key, sizeof(key)) != 0) {
+        cudaGraphExecDestroy(p.vgraph);
+        p.vgraph = nullptr;
+    }
+    Level& Lf = p.lv[p.L];
+    if (!p.vgraph) {
+        if (!p.cap_stream) JFNK_CUDA_TRY(cudaStreamCreateWithFlags(&p.cap_stream, cudaStreamNonBlocking));
+        long long nF0[JFNK_MAX_LEVELS];
+        memcpy(nF0, p.nF, sizeof(nF0));
+        const long long l0 = g_launches;
+        JFNK_CUDA_TRY(cudaStreamBeginCapture(p.cap_stream, cudaStreamCaptureModeThreadLocal));
+        jfnk_status s = vcycle<T>(p, o, p.L, as<T>(Lf.b), as<T>(Lf.s), p.cap_stream);
+        cudaGraph_t graph = nullptr;
+        cudaError_t e = cudaStreamEndCapture(p.cap_stream, &graph);
+        if (s != JFNK_OK) {
+            if (e == cudaSuccess && graph) cudaGraphDestroy(graph);
+            return s;
+        }
+        JFNK_CUDA_TRY(e);
+        cudaError_t ei = cudaGraphInstantiate(&p.vgraph, graph, 0);
+        cudaGraphDestroy(graph);
+        JFNK_CUDA_TRY(ei);
+        for (int l = 0; l < JFNK_MAX_LEVELS; ++l) p.vgraph_nF[l] = p.nF[l] - nF0[l];
+        memcpy(p.nF, nF0, sizeof(nF0));  // the captured launches have not run
+        p.vgraph_launches = g_launches - l0;
+        g_launches = l0;
+        memcpy(p.vgraph_key, key, sizeof(key));
+    }
+    JFNK_CUDA_TRY(cudaGraphLaunch(p.vgraph, st));
+    for (int l = 0; l < JFNK_MAX_LEVELS; ++l) p.nF[l] += p.vgraph_nF[l];
+    g_launches += p.vgraph_launches;
     return JFNK_OK;
 }
 
@@ -399,7 +469,7 @@ static jfnk_status mg_setup_T(P& p, const jfnk_options& o, const double* u, int 
             a.out = as<T>(L.pw);
             a.red = RedOut::NORM;
             a.red_norm = L.nrm1;
-            JFNK_TRY(launch_stencil<T>(prob_of(p), Mode::JV, a, st));
+            JFNK_TRY(launch_op<T>(p, Mode::JV, a, st));
             p.nF[l]++;
             // lambda = ||J v|| / ||v||; v <- J v / ||J v||
             JFNK_TRY(ratio_scalar(L.lam, L.nrm1, L.nrm0, st));
@@ -441,9 +511,18 @@ static jfnk_status read_norm(P& p, const double* v, double* host, cudaStream_t s
     return JFNK_OK;
 }
 
-// w = J(u) v in FP64 with the paper's eps (Sec. 1); Au = A(u)
+// w = J(u) v in FP64 with the paper's eps (Sec. 1); Au = A(u).  In the adjoint
+// solve w = J(u)^T v (exact vector-Jacobian product).
 static jfnk_status jv64(P& p, const double* u, const double* Au, const double* v, double* w, cudaStream_t st) {
     const Grid& g = p.lv[p.L].g;
+    if (p.adj) {
+        StencilArgs<double> a = base_args<double>(p, p.L);
+        a.u = u;
+        a.v = v;
+        a.out = w;
+        p.nF[p.L]++;
+        return launch_vjp<double>(prob_of(p), Mode::JV, a, st);
+    }
     EpsParams ep;
     ep.mode = JFNK_EPS_PAPER;
     ep.n_unknowns = (double)g.interior();
@@ -506,7 +585,12 @@ static jfnk_status fgmres(P& p, const jfnk_options& o, const double* u, double e
             T* zj = Z + (size_t)j * N;
             // z_j = MG(v_j)
             JFNK_TRY((cast_copy<T, double>(as<T>(Lf.b), vj, N, st)));
-            JFNK_TRY(vcycle<T>(p, o, p.L, as<T>(Lf.b), zj, st));
+            if (o.use_graph && !prof_on()) {
+                JFNK_TRY(vcycle_graph<T>(p, o, st));
+                JFNK_CUDA_TRY(cudaMemcpyAsync(zj, Lf.s, sizeof(T) * N, cudaMemcpyDeviceToDevice, st));
+            } else {
+                JFNK_TRY(vcycle<T>(p, o, p.L, as<T>(Lf.b), zj, st));
+            }
             // w = J z_j  (FP64)
             const double* z64 = nullptr;
             if (sizeof(T) == 8) {
@@ -777,6 +861,7 @@ void jfnk_default_options(jfnk_options* o) {
     o->line_search = 1;
     o->ls_max = 10;
     o->seed = 0;
+    o->use_graph = 1;
 }
 
 jfnk_status jfnk_problem_create(const jfnk_problem_desc* desc, jfnk_problem** out) {
@@ -824,6 +909,10 @@ jfnk_status jfnk_problem_create(const jfnk_problem_desc* desc, jfnk_problem** ou
 }
 
 jfnk_status jfnk_problem_destroy(jfnk_problem* p) {
+    if (p) {
+        if (p->vgraph) cudaGraphExecDestroy(p->vgraph);
+        if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
+    }
     delete p;
     return JFNK_OK;
 }
@@ -877,6 +966,10 @@ jfnk_status jfnk_set_workspace(jfnk_problem* p, const jfnk_options* opts, void* 
         return JFNK_ERR_WORKSPACE;
     }
     plan(*p, base, opts);
+    if (p->vgraph) {  // the captured cycle refers to the previous workspace
+        cudaGraphExecDestroy(p->vgraph);
+        p->vgraph = nullptr;
+    }
     p->ws = base;
     p->ws_bytes = need;
     p->has_solver = opts != nullptr;
@@ -1113,4 +1206,117 @@ jfnk_status jfnk_level_vector(jfnk_problem* p, int level, int which, void* out, 
     const size_t esz = p->pc == JFNK_F32 ? 4 : 8;
     JFNK_CUDA_TRY(cudaMemcpyAsync(out, src, esz * L.g.size, cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
     return JFNK_OK;
+}
+
+// ---- adjoint (vector-Jacobian products, adjoint solve) --------------------
+
+template <typename T>
+static jfnk_status vjp_T(P* p, int level, const T* u, const T* w, T* JTw, T* dk, cudaStream_t st) {
+    StencilArgs<T> a = base_args<T>(*p, level);
+    a.u = u;
+    a.v = w;
+    a.out = JTw;
+    a.dkout = dk;
+    a.dk_scale = (T)(1.5 * p->lv[level].h);  // (dF/dkappa_e)^T w = (3h/2) x element sum
+    return launch_vjp<T>(prob_of(*p), Mode::JV, a, st);
+}
+
+jfnk_status jfnk_vjp(jfnk_problem* p, int level, int dtype, const void* u, const void* w, void* JTw,
+                     void* dFdkappa_w, void* stream) {
+    JFNK_TRY(check_level(p, level, dtype));
+    if (!u || !w || !JTw || p->desc.kind == JFNK_BRATU2D) {
+        set_error("jfnk_vjp: null vector or 2D problem (Bratu's J is symmetric: use jfnk_jvp)");
+        return JFNK_ERR_INVALID_ARG;
+    }
+    if (dFdkappa_w && p->desc.kind != JFNK_NDK3D) {
+        set_error("dF/dkappa exists for the coefficient problem only");
+        return JFNK_ERR_INVALID_ARG;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    if (dtype == JFNK_F64)
+        return vjp_T<double>(p, level, (const double*)u, (const double*)w, (double*)JTw, (double*)dFdkappa_w, st);
+    return vjp_T<float>(p, level, (const float*)u, (const float*)w, (float*)JTw, (float*)dFdkappa_w, st);
+}
+
+jfnk_status jfnk_set_kappa(jfnk_problem* p, const double* kappa, void* stream) {
+    if (!p || !p->bound || !kappa || p->desc.kind != JFNK_NDK3D) {
+        set_error("jfnk_set_kappa: needs a bound coefficient problem and a kappa pointer");
+        return JFNK_ERR_INVALID_ARG;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    Level& Lf = p->lv[p->L];
+    const size_t ne = (size_t)Lf.g.n * Lf.g.n * Lf.g.n;
+    JFNK_CUDA_TRY(cudaMemcpyAsync(Lf.kappa64, kappa, ne * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    for (int l = p->L; l >= 1; --l) JFNK_TRY(coarsen_kappa(p->lv[l - 1].g.n, p->lv[l].kappa64, p->lv[l - 1].kappa64, st));
+    for (int l = 0; l <= p->L; ++l) {
+        const long long nel = (long long)p->lv[l].g.n * p->lv[l].g.n * p->lv[l].g.n;
+        JFNK_TRY((cast_copy<float, double>(p->lv[l].kappa32, p->lv[l].kappa64, nel, st)));
+    }
+    for (auto& L : p->lv) L.pv_valid = false;
+    return JFNK_OK;
+}
+
+template <typename T>
+static jfnk_status adjoint_T(P& p, const jfnk_options& o, const double* u, const double* g, double* lambda,
+                             double* grad_kappa, double rtol, jfnk_stats* stats, cudaStream_t st) {
+    auto t0 = std::chrono::steady_clock::now();
+    struct AdjGuard {
+        P& q;
+        explicit AdjGuard(P& qq) : q(qq) { q.adj = true; }
+        ~AdjGuard() { q.adj = false; }
+    } guard(p);
+    for (int l = 0; l <= p.L; ++l) p.nF[l] = 0;
+    const Grid& gf = p.lv[p.L].g;
+    // hierarchy at u; the power method now estimates lambda of J^T (same spectrum as J)
+    JFNK_TRY(mg_setup_T<T>(p, o, u, 0, st));
+    JFNK_TRY((cast_scale_interior<double, double>(p.rhs64, g, 1.0, gf, st)));
+    int its = 0;
+    JFNK_TRY(fgmres<T>(p, o, u, rtol, its, st));
+    JFNK_TRY(check_status(p, st));
+    JFNK_CUDA_TRY(cudaMemcpyAsync(lambda, p.delta, sizeof(double) * gf.size, cudaMemcpyDeviceToDevice, st));
+    if (grad_kappa) {
+        // grad_kappa = -(dF/dkappa)^T lambda  (F(u(kappa), kappa) = 0)
+        StencilArgs<double> a = base_args<double>(p, p.L);
+        a.u = u;
+        a.v = p.delta;
+        a.out = p.w64;
+        a.dkout = grad_kappa;
+        a.dk_scale = -1.5 * p.lv[p.L].h;
+        JFNK_TRY(launch_vjp<double>(prob_of(p), Mode::JV, a, st));
+    }
+    JFNK_CUDA_TRY(cudaStreamSynchronize(st));
+    if (stats) {
+        jfnk_stats S;
+        memset(&S, 0, sizeof(S));
+        S.linear_its = its;
+        S.lin_hist[0] = its;
+        S.converged = 1;
+        double ge = 0.0;
+        for (int l = 0; l <= p.L && l < JFNK_MAX_LEVELS; ++l) {
+            S.nF[l] = p.nF[l];
+            ge += std::pow(2.0, -(double)p.d * (p.L - l)) * (double)p.nF[l];
+            if (l >= 1) JFNK_CUDA_TRY(cudaMemcpy(&S.lambda_max[l], p.lv[l].lam, sizeof(double), cudaMemcpyDeviceToHost));
+        }
+        S.ge = ge;
+        S.status = JFNK_OK;
+        S.solve_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+        *stats = S;
+    }
+    return JFNK_OK;
+}
+
+jfnk_status jfnk_adjoint_solve(jfnk_problem* p, const jfnk_options* opts, const double* u, const double* g,
+                               double* lambda, double* grad_kappa, double rtol, jfnk_stats* stats, void* stream) {
+    JFNK_TRY(need_solver(p, opts));
+    if (!u || !g || !lambda || p->desc.kind == JFNK_BRATU2D || !(rtol > 0.0)) {
+        set_error("jfnk_adjoint_solve: invalid arguments (3D diffusion problems only, rtol > 0)");
+        return JFNK_ERR_INVALID_ARG;
+    }
+    if (grad_kappa && p->desc.kind != JFNK_NDK3D) {
+        set_error("grad_kappa exists for the coefficient problem only");
+        return JFNK_ERR_INVALID_ARG;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    if (p->pc == JFNK_F32) return adjoint_T<float>(*p, *opts, u, g, lambda, grad_kappa, rtol, stats, st);
+    return adjoint_T<double>(*p, *opts, u, g, lambda, grad_kappa, rtol, stats, st);
 }

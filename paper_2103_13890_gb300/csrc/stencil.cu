@@ -17,6 +17,7 @@
 
 #include "element.cuh"
 #include "profile.cuh"
+#include "stencil_v2.cuh"
 #include "reduce.cuh"
 #include "stencil.cuh"
 
@@ -375,6 +376,8 @@ static jfnk_status dispatch_mode(Mode mode, const StencilArgs<T>& a, cudaStream_
 
 template <typename T>
 static jfnk_status launch_stencil_impl(Prob prob, Mode mode, const StencilArgs<T>& a, cudaStream_t st) {
+    if (prob != Prob::BRATU2 && a.face != nullptr && v2_applicable(a.g))
+        return launch_stencil_v2<T>(prob, mode, a, st);
     switch (prob) {
         case Prob::BRATU2: return dispatch_mode<T, Prob::BRATU2>(mode, a, st);
         case Prob::ND3: return dispatch_mode<T, Prob::ND3>(mode, a, st);

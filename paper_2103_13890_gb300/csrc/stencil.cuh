@@ -70,7 +70,18 @@ struct StencilArgs {
     EpsSlot* red_eps;    // EPS: FD step of the reduced vector
     EpsParams epsp;
     int* status;         // device status word (non-finite eps)
+    // face buffer of the halo-free 3D kernel (nullable: then the tiled kernel runs)
+    T* face;
+    long long face_cap;
+    // adjoint kernel: per-element (dF/dkappa_e)^T v times dk_scale (nullable)
+    T* dkout;
+    T dk_scale;
 };
+
+// Adjoint operator: the same fused modes with J^T v (vector-Jacobian product,
+// exact) in place of the FD action; Mode::JV writes J^T v.
+template <typename T>
+jfnk_status launch_vjp(Prob prob, Mode mode, const StencilArgs<T>& a, cudaStream_t st);
 
 template <typename T>
 jfnk_status launch_stencil(Prob prob, Mode mode, const StencilArgs<T>& a, cudaStream_t st);

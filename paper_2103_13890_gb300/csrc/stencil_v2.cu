@@ -1,0 +1,488 @@
+// 3D element-residual kernel without halo recomputation (grids with n a
+// multiple of 32, n >= 64).
+//
+// A CTA of n x BY threads (n * BY = 1024) owns the elements of BY full x-rows
+// [y0, y0+BY) on the layers of one z chunk [z0, z1): every element of the grid
+// is evaluated exactly once and every warp is full.  Thread (x, w) evaluates the
+// element with lower corner (x, y0+w, k) on each layer k; node planes live in a
+// three-plane shared ring (the plane after next is prefetched into registers
+// while the current layer is computed) and the element contributions are
+// exchanged through shared memory.  A node's total is
+//     lo(layer k) + hi(layer k-1),
+// summed over the 2^2 elements around it in the xy plane in a fixed order; the
+// hi part is carried in a register from one layer to the next.
+//
+// Nodes on internal tile faces -- the node rows y0 and y0+BY shared with the
+// neighbouring y tiles and the planes z0 and z1 shared with the neighbouring z
+// chunks -- receive only part of their element contributions in this CTA.  The
+// CTA stores those partial sums in a face buffer, and stencil3d_fixup_kernel
+// adds the two (four on an edge) partials in a fixed order and applies the same
+// epilogue.  The fixup kernel also completes the norm reduction, so results are
+// deterministic.  Every F_i is still the sum of the same element integrals.
+#include <algorithm>
+#include <cstdio>
+
+#include "element.cuh"
+#include "reduce.cuh"
+#include "stencil.cuh"
+#include "stencil_v2.cuh"
+
+namespace jfnk {
+
+template <typename T>
+__device__ __forceinline__ T eps_of2(const EpsSlot* s);
+template <>
+__device__ __forceinline__ double eps_of2<double>(const EpsSlot* s) { return s->e; }
+template <>
+__device__ __forceinline__ float eps_of2<float>(const EpsSlot* s) { return s->ef; }
+template <typename T>
+__device__ __forceinline__ T inv_eps_of2(const EpsSlot* s);
+template <>
+__device__ __forceinline__ double inv_eps_of2<double>(const EpsSlot* s) { return s->inv; }
+template <>
+__device__ __forceinline__ float inv_eps_of2<float>(const EpsSlot* s) { return s->invf; }
+
+template <typename T>
+struct ChebK2 {
+    T theta_inv, c1, c2;
+};
+template <typename T>
+__device__ __forceinline__ ChebK2<T> cheb_of2(const ChebTable* t, int i);
+template <>
+__device__ __forceinline__ ChebK2<double> cheb_of2<double>(const ChebTable* t, int i) {
+    return {t->theta_inv, t->c1[i], t->c2[i]};
+}
+template <>
+__device__ __forceinline__ ChebK2<float> cheb_of2<float>(const ChebTable* t, int i) {
+    return {t->theta_invf, t->c1f[i], t->c2f[i]};
+}
+
+// Per-node epilogue (same definitions as the tiled kernel's): val = A(w)_i.
+template <typename T, Mode M>
+__device__ __forceinline__ void epilogue2(const StencilArgs<T>& a, long long idx, bool inner, T val, T inv_eps,
+                                          const ChebK2<T>& ck, float& red) {
+    if (M == Mode::F) {
+        T f = T(0), av = T(0);
+        if (inner) {
+            av = val;
+            f = val - (T)a.load_const;
+            if (a.load) f -= a.load[idx];
+        }
+        a.out[idx] = f;
+        if (a.out2) a.out2[idx] = av;
+        red += (float)f * (float)f;
+    } else if (M == Mode::JV) {
+        T jv = T(0);
+        if (inner) {
+            T aw = val - (T)a.load_const;
+            if (a.load) aw -= a.load[idx];
+            jv = (aw - a.Au[idx]) * inv_eps;
+        }
+        a.out[idx] = jv;
+        red += (float)jv * (float)jv;
+    } else if (M == Mode::BMJ) {
+        T o = inner ? a.rhs[idx] - (val - a.Au[idx]) * inv_eps : T(0);
+        a.out[idx] = o;
+        red += (float)o * (float)o;
+    } else if (M == Mode::CHEB0) {
+        T rr = T(0), dd = T(0);
+        if (inner) {
+            rr = a.rhs[idx] - (val - a.Au[idx]) * inv_eps;
+            dd = rr * ck.theta_inv;
+        }
+        a.out[idx] = rr;
+        a.out2[idx] = dd;
+        red += (float)dd * (float)dd;
+    } else if (M == Mode::CHEB) {
+        T rr = T(0), ss = T(0), dn = T(0);
+        if (inner) {
+            T jd = (val - a.Au[idx]) * inv_eps;
+            T dc = a.v[idx];
+            rr = a.r[idx] - jd;
+            ss = a.s[idx] + dc;
+            dn = ck.c1 * dc + ck.c2 * rr;
+        }
+        a.r[idx] = rr;
+        a.s[idx] = ss;
+        a.dnew[idx] = dn;
+        red += (float)dn * (float)dn;
+    } else {  // CHEBLAST
+        T ss = T(0);
+        if (inner) {
+            T jd = (val - a.Au[idx]) * inv_eps;
+            T dc = a.v[idx];
+            T rr = a.r[idx] - jd;
+            T dn = ck.c1 * dc + ck.c2 * rr;
+            ss = a.s[idx] + dc + dn;
+        }
+        a.s[idx] = ss;
+        red += (float)ss * (float)ss;
+    }
+}
+
+// Face buffer addressing
+__device__ __forceinline__ long long ylo_idx(const V2Geom& q, int ty, int c, int zl, int x) {
+    return q.ylo + (((long long)ty * q.Tz + c) * (q.ZC + 1) + zl) * (q.n + 1) + x;
+}
+__device__ __forceinline__ long long yhi_idx(const V2Geom& q, int ty, int c, int zl, int x) {
+    return q.yhi + (((long long)ty * q.Tz + c) * (q.ZC + 1) + zl) * (q.n + 1) + x;
+}
+__device__ __forceinline__ long long zlo_idx(const V2Geom& q, int ty, int c, int w, int x) {
+    return q.zlo + (((long long)ty * q.Tz + c) * (q.BY + 1) + w) * (q.n + 1) + x;
+}
+__device__ __forceinline__ long long zhi_idx(const V2Geom& q, int ty, int c, int w, int x) {
+    return q.zhi + (((long long)ty * q.Tz + c) * (q.BY + 1) + w) * (q.n + 1) + x;
+}
+
+template <typename T, Prob P, Mode M>
+__global__ void __launch_bounds__(kV2Threads, 1) stencil3d_v2_kernel(const StencilArgs<T> a, const V2Geom q) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int n = q.n, BY = q.BY, NP = n + 1;
+    T* W = reinterpret_cast<T*>(smem_raw);  // [3][BY+1][n+1]
+    T* C = W + 3 * (BY + 1) * NP;           // [8][BY][n]
+    __shared__ double red_sm[32];
+    const Grid g = a.g;
+    const int tx = threadIdx.x, w = threadIdx.y;
+    const int ty = blockIdx.x, c = blockIdx.y;
+    const int y0 = ty * BY;
+    const int z0 = c * q.ZC;
+    const int z1 = min(z0 + q.ZC, n);
+    T eps = T(0), inv_eps = T(0);
+    if (M != Mode::F) {
+        eps = eps_of2<T>(a.eps);
+        inv_eps = inv_eps_of2<T>(a.eps);
+    }
+    ChebK2<T> ck = {T(0), T(0), T(0)};
+    if (M == Mode::CHEB0 || M == Mode::CHEB || M == Mode::CHEBLAST) ck = cheb_of2<T>(a.cheb, a.cheb_step);
+
+    // nodal value of w = x + eps v at (x, y, z); boundary entries of v ignored
+    auto node_val = [&](int x, int y, int z) -> T {
+        const long long idx = (long long)z * g.sz + (long long)y * g.sy + x;
+        T val = a.u[idx];
+        if (M != Mode::F) {
+            const bool bnd = x == 0 || x == n || y == 0 || y == n || z == 0 || z == n;
+            if (!bnd) val += eps * a.v[idx];
+        }
+        return val;
+    };
+    // this thread's share of a plane: (tx, y0+w); row y0+BY (w == 0); column n (tx == n-1)
+    const bool extra_row = (w == 0);
+    const bool extra_col = (tx == n - 1);
+    auto load4 = [&](int z, T& p0, T& p1, T& p2, T& p3) {
+        p0 = node_val(tx, y0 + w, z);
+        if (extra_col) p1 = node_val(n, y0 + w, z);
+        if (extra_row) p2 = node_val(tx, y0 + BY, z);
+        if (extra_row && extra_col) p3 = node_val(n, y0 + BY, z);
+    };
+    auto store4 = [&](int buf, T p0, T p1, T p2, T p3) {
+        T* Wb = W + buf * (BY + 1) * NP;
+        Wb[w * NP + tx] = p0;
+        if (extra_col) Wb[w * NP + n] = p1;
+        if (extra_row) Wb[BY * NP + tx] = p2;
+        if (extra_row && extra_col) Wb[BY * NP + n] = p3;
+    };
+
+    T q0 = T(0), q1 = T(0), q2 = T(0), q3 = T(0);
+    load4(z0, q0, q1, q2, q3);
+    store4(z0 % 3, q0, q1, q2, q3);
+    load4(z0 + 1, q0, q1, q2, q3);
+    store4((z0 + 1) % 3, q0, q1, q2, q3);
+    __syncthreads();
+
+    // rows handled by this thread: own row y0+w, and for w == 0 also row y0+BY
+    const int yA = y0 + w, yB = y0 + BY;
+    const bool faceA = (w == 0) && y0 > 0;         // shared with the tile below
+    const bool bndA = (yA == 0);
+    const bool faceB = yB < n;                      // shared with the tile above
+    const bool bndB = yB == n;
+    T carryA = T(0), carryB = T(0);
+    float red = 0.f;
+    const T scale = a.node_scale;
+    const T zero = T(0);
+    const ChebK2<T> ck0 = ck;
+
+    for (int k = z0; k < z1; ++k) {
+        const bool pf = (k + 2 <= z1);
+        if (pf) load4(k + 2, q0, q1, q2, q3);
+        const T* W0 = W + (k % 3) * (BY + 1) * NP;
+        const T* W1 = W + ((k + 1) % 3) * (BY + 1) * NP;
+        T ue[8] = {W0[w * NP + tx],       W0[w * NP + tx + 1],       W0[(w + 1) * NP + tx],
+                   W0[(w + 1) * NP + tx + 1], W1[w * NP + tx],       W1[w * NP + tx + 1],
+                   W1[(w + 1) * NP + tx],     W1[(w + 1) * NP + tx + 1]};
+        T r[8];
+        if (P == Prob::NDK3)
+            elem_nd3<T, true>(ue, a.kappa[((long long)k * n + (y0 + w)) * n + tx], r);
+        else
+            elem_nd3<T, false>(ue, T(1), r);
+#pragma unroll
+        for (int cc = 0; cc < 8; ++cc) C[(cc * BY + w) * n + tx] = r[cc];
+        __syncthreads();
+        // own row y0+w: b = 0 corners of row w, b = 1 corners of row w-1
+        T loA = C[(0 * BY + w) * n + tx];
+        T hiA = C[(4 * BY + w) * n + tx];
+        if (tx > 0) {
+            loA += C[(1 * BY + w) * n + tx - 1];
+            hiA += C[(5 * BY + w) * n + tx - 1];
+        }
+        if (w > 0) {
+            loA += C[(2 * BY + w - 1) * n + tx];
+            hiA += C[(6 * BY + w - 1) * n + tx];
+            if (tx > 0) {
+                loA += C[(3 * BY + w - 1) * n + tx - 1];
+                hiA += C[(7 * BY + w - 1) * n + tx - 1];
+            }
+        }
+        T loB = T(0), hiB = T(0);
+        if (extra_row) {  // row y0+BY: b = 1 corners of row BY-1
+            loB = C[(2 * BY + BY - 1) * n + tx];
+            hiB = C[(6 * BY + BY - 1) * n + tx];
+            if (tx > 0) {
+                loB += C[(3 * BY + BY - 1) * n + tx - 1];
+                hiB += C[(7 * BY + BY - 1) * n + tx - 1];
+            }
+        }
+        // plane k
+        {
+            const T vA = loA + carryA;
+            const long long idx = (long long)k * g.sz + (long long)yA * g.sy + tx;
+            if (k == 0 || bndA || tx == 0) {
+                epilogue2<T, M>(a, idx, false, zero, inv_eps, ck0, red);
+            } else if (faceA) {
+                a.face[ylo_idx(q, ty, c, k - z0, tx)] = vA;
+            } else if (k == z0) {
+                a.face[zlo_idx(q, ty, c, w, tx)] = vA;
+            } else {
+                epilogue2<T, M>(a, idx, true, vA * scale, inv_eps, ck0, red);
+            }
+            if (extra_col) epilogue2<T, M>(a, idx + 1, false, zero, inv_eps, ck0, red);  // x = n
+            carryA = hiA;
+        }
+        if (extra_row) {
+            const T vB = loB + carryB;
+            const long long idx = (long long)k * g.sz + (long long)yB * g.sy + tx;
+            if (k == 0 || bndB || tx == 0) {
+                epilogue2<T, M>(a, idx, false, zero, inv_eps, ck0, red);
+            } else {
+                a.face[yhi_idx(q, ty, c, k - z0, tx)] = vB;
+            }
+            if (extra_col) epilogue2<T, M>(a, idx + 1, false, zero, inv_eps, ck0, red);
+            carryB = hiB;
+        }
+        __syncthreads();
+        if (pf) store4((k + 2) % 3, q0, q1, q2, q3);
+        __syncthreads();
+    }
+    // plane z1: the carries are partial sums from the last layer only
+    {
+        const long long idx = (long long)z1 * g.sz + (long long)yA * g.sy + tx;
+        if (z1 == n || bndA || tx == 0) {
+            epilogue2<T, M>(a, idx, false, zero, inv_eps, ck0, red);
+        } else if (faceA) {
+            a.face[ylo_idx(q, ty, c, z1 - z0, tx)] = carryA;
+        } else {
+            a.face[zhi_idx(q, ty, c, w, tx)] = carryA;
+        }
+        if (extra_col) epilogue2<T, M>(a, idx + 1, false, zero, inv_eps, ck0, red);
+        if (extra_row) {
+            const long long idxB = (long long)z1 * g.sz + (long long)yB * g.sy + tx;
+            if (z1 == n || bndB || tx == 0) {
+                epilogue2<T, M>(a, idxB, false, zero, inv_eps, ck0, red);
+            } else {
+                a.face[yhi_idx(q, ty, c, z1 - z0, tx)] = carryB;
+            }
+            if (extra_col) epilogue2<T, M>(a, idxB + 1, false, zero, inv_eps, ck0, red);
+        }
+    }
+    // block partial of the norm; the fixup kernel completes the reduction
+    if (a.red != RedOut::NONE) {
+        const double bs = block_sum(red, red_sm);
+        if (threadIdx.x == 0 && threadIdx.y == 0) a.partials[blockIdx.x + gridDim.x * blockIdx.y] = bs;
+    }
+}
+
+template <typename T, Mode M>
+__global__ void __launch_bounds__(256) stencil3d_fixup_kernel(const StencilArgs<T> a, const V2Geom q, int main_blocks) {
+    __shared__ double red_sm[32];
+    const Grid g = a.g;
+    const int n = q.n, BY = q.BY, ZC = q.ZC;
+    const long long m1 = n - 1;
+    const long long countA = (long long)(q.Ty - 1) * m1 * m1;
+    const long long rowsB = m1 - (q.Ty - 1);
+    const long long countB = (long long)(q.Tz - 1) * rowsB * m1;
+    T inv_eps = T(0);
+    if (M != Mode::F) inv_eps = inv_eps_of2<T>(a.eps);
+    ChebK2<T> ck = {T(0), T(0), T(0)};
+    if (M == Mode::CHEB0 || M == Mode::CHEB || M == Mode::CHEBLAST) ck = cheb_of2<T>(a.cheb, a.cheb_step);
+    float red = 0.f;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < countA + countB;
+         i += (long long)gridDim.x * blockDim.x) {
+        int x, y, z;
+        T total;
+        if (i < countA) {
+            const int tyb = (int)(i / (m1 * m1)) + 1;
+            const long long rem = i % (m1 * m1);
+            z = (int)(rem / m1) + 1;
+            x = (int)(rem % m1) + 1;
+            y = tyb * BY;
+            const int cz = z / ZC, zl = z - cz * ZC;
+            if (zl != 0) {
+                total = a.face[yhi_idx(q, tyb - 1, cz, zl, x)] + a.face[ylo_idx(q, tyb, cz, zl, x)];
+            } else {
+                total = (a.face[yhi_idx(q, tyb - 1, cz - 1, ZC, x)] + a.face[ylo_idx(q, tyb, cz - 1, ZC, x)]) +
+                        (a.face[yhi_idx(q, tyb - 1, cz, 0, x)] + a.face[ylo_idx(q, tyb, cz, 0, x)]);
+            }
+        } else {
+            const long long j = i - countA;
+            const int cb = (int)(j / (rowsB * m1)) + 1;
+            const long long rem = j % (rowsB * m1);
+            const int yi = (int)(rem / m1);
+            x = (int)(rem % m1) + 1;
+            y = (yi / (BY - 1)) * BY + (yi % (BY - 1)) + 1;
+            z = cb * ZC;
+            const int tyy = y / BY, ww = y - tyy * BY;
+            total = a.face[zhi_idx(q, tyy, cb - 1, ww, x)] + a.face[zlo_idx(q, tyy, cb, ww, x)];
+        }
+        const long long idx = (long long)z * g.sz + (long long)y * g.sy + x;
+        epilogue2<T, M>(a, idx, true, total * a.node_scale, inv_eps, ck, red);
+    }
+    if (a.red == RedOut::NONE) return;
+    const double bs = block_sum(red, red_sm);
+    __shared__ int s_last;
+    const int tid = threadIdx.x;
+    if (tid == 0) {
+        a.partials[main_blocks + blockIdx.x] = bs;
+        __threadfence();
+        const unsigned int prev = atomicAdd(a.counter, 1u);
+        s_last = (prev == gridDim.x - 1) ? 1 : 0;
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    const int total_blocks = main_blocks + gridDim.x;
+    double s = 0.0;
+    for (int b = tid; b < total_blocks; b += blockDim.x) s += __ldcg(&a.partials[b]);
+    s = block_sum(s, red_sm);
+    if (tid == 0) {
+        *a.counter = 0u;
+        const double nrm = sqrt(s);
+        if (a.red_norm) *a.red_norm = nrm;
+        if (a.red == RedOut::EPS) {
+            double e = eps_formula(a.epsp.mode, a.epsp.n_unknowns, *a.epsp.xstat, nrm);
+            double inv = e > 0.0 ? 1.0 / e : 0.0;
+            if (!isfinite(e) || !isfinite(inv)) {
+                if (a.status) atomicOr(a.status, 1);
+                e = 0.0;
+                inv = 0.0;
+            }
+            a.red_eps->e = e;
+            a.red_eps->inv = inv;
+            a.red_eps->ef = (float)e;
+            a.red_eps->invf = (float)inv;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+bool v2_applicable(const Grid& g) {
+    return g.d == 3 && g.n >= 64 && g.n <= 512 && (g.n % 32) == 0;
+}
+
+V2Geom v2_geometry(const Grid& g, int num_sms) {
+    V2Geom q;
+    q.n = g.n;
+    // rows per CTA: the largest divisor of n with n * BY <= kV2Threads, so that
+    // the y tiles cover all n element rows exactly
+    q.BY = kV2Threads / g.n;
+    while (q.BY > 1 && g.n % q.BY != 0) --q.BY;
+    q.Ty = g.n / q.BY;
+    // z chunks: minimise waves x layers per CTA over whole waves of one CTA per SM
+    int best_tz = 1;
+    long long best_cost = -1;
+    for (int tz = 1; tz <= g.n; ++tz) {
+        const int zc = (g.n + tz - 1) / tz;
+        if ((long long)(tz - 1) * zc >= g.n) continue;  // no empty chunk
+        const long long waves = ((long long)q.Ty * tz + num_sms - 1) / num_sms;
+        const long long cost = waves * (zc + 1) * 16 + (tz - 1);  // small preference for fewer faces
+        if (best_cost < 0 || cost < best_cost) {
+            best_cost = cost;
+            best_tz = tz;
+        }
+    }
+    q.Tz = best_tz;
+    q.ZC = (g.n + q.Tz - 1) / q.Tz;
+    const long long ysz = (long long)q.Ty * q.Tz * (q.ZC + 1) * (q.n + 1);
+    const long long zsz = (long long)q.Ty * q.Tz * (q.BY + 1) * (q.n + 1);
+    q.ylo = 0;
+    q.yhi = ysz;
+    q.zlo = 2 * ysz;
+    q.zhi = 2 * ysz + zsz;
+    q.face_count = 2 * ysz + 2 * zsz;
+    return q;
+}
+
+long long v2_face_count(const Grid& g) {
+    if (!v2_applicable(g)) return 0;
+    return v2_geometry(g, kNumSMs).face_count;
+}
+
+static int fixup_blocks(const V2Geom& q) {
+    const long long m1 = q.n - 1;
+    const long long cnt = (long long)(q.Ty - 1) * m1 * m1 + (long long)(q.Tz - 1) * (m1 - (q.Ty - 1)) * m1;
+    long long b = (cnt + 255) / 256;
+    if (b > 4 * kNumSMs) b = 4 * kNumSMs;
+    return (int)(b < 1 ? 1 : b);
+}
+
+template <typename T, Prob P, Mode M>
+static jfnk_status launch_v2_pm(const StencilArgs<T>& a, cudaStream_t st) {
+    const V2Geom q = v2_geometry(a.g, kNumSMs);
+    if (q.face_count > a.face_cap) {
+        set_error("face scratch too small (%lld < %lld)", a.face_cap, q.face_count);
+        return JFNK_ERR_WORKSPACE;
+    }
+    const int main_blocks = q.Ty * q.Tz;
+    const int fb = fixup_blocks(q);
+    if (main_blocks + fb > kMaxRedBlocks * 2) {
+        set_error("v2 grid too large for the reduction scratch");
+        return JFNK_ERR_INVALID_ARG;
+    }
+    const size_t smem = sizeof(T) * (3 * (size_t)(q.BY + 1) * (q.n + 1) + 8 * (size_t)q.BY * q.n);
+    static bool attr_set = false;
+    if (!attr_set) {
+        JFNK_CUDA_TRY(cudaFuncSetAttribute(stencil3d_v2_kernel<T, P, M>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           200 * 1024));
+        attr_set = true;
+    }
+    stencil3d_v2_kernel<T, P, M><<<dim3(q.Ty, q.Tz), dim3(q.n, q.BY), smem, st>>>(a, q);
+    JFNK_LAUNCH_CHECK();
+    stencil3d_fixup_kernel<T, M><<<fb, 256, 0, st>>>(a, q, main_blocks);
+    JFNK_LAUNCH_CHECK();
+    return JFNK_OK;
+}
+
+template <typename T, Prob P>
+static jfnk_status launch_v2_p(Mode mode, const StencilArgs<T>& a, cudaStream_t st) {
+    switch (mode) {
+        case Mode::F: return launch_v2_pm<T, P, Mode::F>(a, st);
+        case Mode::JV: return launch_v2_pm<T, P, Mode::JV>(a, st);
+        case Mode::BMJ: return launch_v2_pm<T, P, Mode::BMJ>(a, st);
+        case Mode::CHEB0: return launch_v2_pm<T, P, Mode::CHEB0>(a, st);
+        case Mode::CHEB: return launch_v2_pm<T, P, Mode::CHEB>(a, st);
+        case Mode::CHEBLAST: return launch_v2_pm<T, P, Mode::CHEBLAST>(a, st);
+    }
+    set_error("unknown stencil mode");
+    return JFNK_ERR_INVALID_ARG;
+}
+
+template <typename T>
+jfnk_status launch_stencil_v2(Prob prob, Mode mode, const StencilArgs<T>& a, cudaStream_t st) {
+    if (prob == Prob::ND3) return launch_v2_p<T, Prob::ND3>(mode, a, st);
+    if (prob == Prob::NDK3) return launch_v2_p<T, Prob::NDK3>(mode, a, st);
+    set_error("v2 kernel is 3D only");
+    return JFNK_ERR_INVALID_ARG;
+}
+
+template jfnk_status launch_stencil_v2<double>(Prob, Mode, const StencilArgs<double>&, cudaStream_t);
+template jfnk_status launch_stencil_v2<float>(Prob, Mode, const StencilArgs<float>&, cudaStream_t);
+
+}  // namespace jfnk

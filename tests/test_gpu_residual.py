@@ -36,8 +36,11 @@ def _kappa(n, seed=3):
 
 
 # sizes span several 31 x 7 (3D) / row-segment (2D) tiles with ragged tails
+# (3D grids with n a multiple of 32 and n >= 64 take the halo-free kernel with
+# its face fixup; the others the tiled kernel)
 CASES = [("bratu2d", 7), ("bratu2d", 64), ("bratu2d", 95), ("bratu2d", 600),
-         ("nd3d", 4), ("nd3d", 33), ("nd3d", 40), ("ndk3d", 5), ("ndk3d", 37)]
+         ("nd3d", 4), ("nd3d", 33), ("nd3d", 40), ("ndk3d", 5), ("ndk3d", 37),
+         ("nd3d", 64), ("nd3d", 96), ("ndk3d", 64)]
 
 
 @pytest.mark.parametrize("kind,n", CASES)
@@ -84,7 +87,7 @@ def _fd_bound(kind, u, v, kap, load, eps):
     return 64 * EPS64 * np.linalg.norm(A_abs) * 2 ** d / eps
 
 
-@pytest.mark.parametrize("kind,n", [("bratu2d", 64), ("bratu2d", 95), ("nd3d", 33), ("ndk3d", 20)])
+@pytest.mark.parametrize("kind,n", [("bratu2d", 64), ("bratu2d", 95), ("nd3d", 33), ("ndk3d", 20), ("nd3d", 64)])
 def test_jvp_fp64_parity(kind, n):
     kap = _kappa(n) if kind == "ndk3d" else None
     load = fem.mms_load(n) if kind == "nd3d" else None
@@ -106,7 +109,7 @@ def test_jvp_fp64_parity(kind, n):
     assert rel(Jv, Jex) <= 1e-5
 
 
-@pytest.mark.parametrize("kind,n", [("bratu2d", 64), ("nd3d", 33)])
+@pytest.mark.parametrize("kind,n", [("bratu2d", 64), ("nd3d", 33), ("nd3d", 64)])
 def test_jvp_fp32_parity(kind, n):
     """FP32 action with the single-precision step eps = sqrt(2^-23)(1+||u||)/||v||
     against the oracle's FP64 evaluation of the same quotient."""
@@ -137,8 +140,8 @@ def test_jvp_explicit_eps_and_zero_direction():
     assert np.all(Jz == 0)
 
 
-def test_residual_deterministic():
-    n = 40
+@pytest.mark.parametrize("n", [40, 128])
+def test_residual_deterministic(n):
     p = _problem("nd3d", n)
     ud = dev(_state("nd3d", n, seed=5))
     a = host(p.residual(ud))
