@@ -160,6 +160,79 @@ def reference_arm(args):
 
 
 # ---------------------------------------------------------------------------
+# Extras
+# ---------------------------------------------------------------------------
+def batched_extra(jf, torch):
+    """64 independent Bratu instances of uneven sizes solved in one batched call
+    vs one after another (wall clock, inputs resident)."""
+    import math
+    from workloads import batch_instances
+    inst = batch_instances(64, seed=4)
+    ob = jf.default_options(rtol_newton=1e-8, pc_dtype=jf.F32, eps_mode_pc=jf.EPS_FP32)
+    lv = lambda nn: int(round(math.log2(nn // 8))) + 1
+    bps = [jf.Problem("bratu2d", nn, lv(nn), lam=lam, options=ob) for nn, lam in inst]
+    bus = [torch.zeros((nn + 1, nn + 1), dtype=torch.float64, device="cuda") for nn, _ in inst]
+
+    def run_batch():
+        for x in bus:
+            x.zero_()
+        return jf.solve_batched(bps, bus, ob)
+
+    def run_seq():
+        for p_, x in zip(bps, bus):
+            x.zero_()
+            p_.solve(x)
+
+    run_batch()
+    run_seq()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    bst = run_batch()
+    torch.cuda.synchronize()
+    t_batch = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    run_seq()
+    torch.cuda.synchronize()
+    t_seq = time.perf_counter() - t0
+    return {"workload": "64 x bratu2d, n in {129^2, 257^2, 513^2} nodes, lambda~U[1,6.5] seed 4, FP32 PC, rtol 1e-8",
+            "nodes": int(sum((nn + 1) ** 2 for nn, _ in inst)), "batched_s": t_batch, "sequential_s": t_seq,
+            "speedup": t_seq / t_batch, "converged": int(sum(s["converged"] for s in bst)),
+            "max_newton_its": max(s["newton_its"] for s in bst)}
+
+
+def adjoint_extra(jf, torch, n, shape, stream):
+    """Forward solve and multigrid-preconditioned adjoint solve of the
+    coefficient problem at the bench size (CUDA events)."""
+    from workloads import kappa_field, noise_like
+    kap = torch.as_tensor(kappa_field(n, seed=5))
+    oa = jf.default_options(nu_pre=2, nu_post=2, cheb_degree=4, rtol_newton=1e-8, pc_dtype=jf.F32,
+                            eps_mode_pc=jf.EPS_FP32)
+    pa = jf.Problem("ndk3d", n, LEVELS, kappa=kap, options=oa)
+    pa.set_kappa(torch.as_tensor(kappa_field(n, seed=6)))
+    u_obs = torch.zeros(shape, dtype=torch.float64, device="cuda")
+    pa.solve(u_obs)
+    u_obs += torch.as_tensor(noise_like(u_obs.cpu().numpy(), 0.01, seed=7)).cuda()
+    pa.set_kappa(kap)
+    ua = torch.zeros(shape, dtype=torch.float64, device="cuda")
+    for _ in range(2):
+        ua.zero_()
+        pa.solve(ua)
+        pa.adjoint_solve(ua, ua - u_obs, rtol=1e-8)
+    torch.cuda.synchronize()
+    ea, eb, ec = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+    ea.record(stream)
+    ua.zero_()
+    pa.solve(ua)
+    eb.record(stream)
+    _, _, ast = pa.adjoint_solve(ua, ua - u_obs, rtol=1e-8)
+    ec.record(stream)
+    torch.cuda.synchronize()
+    return {"workload": "ndk3d 129^3, kappa = exp(GRF) seed 5, loss 1/2||u-u_obs||^2, FP32 PC, rtol 1e-8",
+            "forward_s": ea.elapsed_time(eb) * 1e-3, "adjoint_s": eb.elapsed_time(ec) * 1e-3,
+            "adjoint_fgmres_its": ast["linear_its"]}
+
+
+# ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
 def main():
@@ -168,7 +241,6 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         return reference_arm(args)
@@ -289,6 +361,10 @@ def main():
         resid[name] = {"dof_per_s": dof / t, "ms": t * 1e3, "achieved_gbs": byts / t / 1e9,
                        "pct_hbm": 100.0 * byts / t / 1e9 / hbm}
 
+    # ---- batched workload and adjoint workload ---------------------------------
+    batch = batched_extra(jf, torch)
+    adj = adjoint_extra(jf, torch, n, shape, stream)
+
     # ---- roofline of the dominant kernel ---------------------------------------
     top = max(prof.items(), key=lambda kv: kv[1][1]) if prof else None
     roof = None
@@ -306,7 +382,7 @@ def main():
                 "peak_source": "measured fp64 pipe rate of this pool's GB300 (bench docstring)"}
 
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1:
         s = oracle_sample(reps=2)
         cpu = {"value": s["estimate_s"], "unit": "s", "cores": 1, "kind": "oracle", "sample": s["sample"]}
 
@@ -326,6 +402,8 @@ def main():
                         "newton_its": st32["newton_its"], "fgmres_its": st32["linear_its"],
                         "rel_diff_vs_fp64_solution": sol_diff},
             "residual_eval": resid,
+            "batched": batch,
+            "adjoint": adj,
             "e2e": {"value": e2e_ms * 1e-3, "unit": "s", "h2d_bytes_per_step": 8 * N, "d2h_bytes_per_step": 8 * N},
             "gpu_launches": int(launches),
             "roofline": roof,

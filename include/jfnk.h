@@ -166,6 +166,20 @@ jfnk_status jfnk_mg_vcycle(jfnk_problem* p, const jfnk_options* opts, const doub
  * on the boundary and receives the solution.  stats may be NULL. */
 jfnk_status jfnk_solve(jfnk_problem* p, const jfnk_options* opts, double* u_inout, jfnk_stats* stats, void* stream);
 
+/* Batched solve of `count` independent 2D Bratu problems of uneven sizes and
+ * parameters (e.g. 129^2 / 257^2 / 513^2 nodes, different lambda) whose
+ * hierarchies end at the same coarse grid.  Each problem keeps its own
+ * workspace (laid out for opts); u_inout[i] is instance i's iterate.  The
+ * instances advance in lock step (Newton, FGMRES(m), line search per
+ * instance), and every device operation is one launch over all instances it
+ * applies to -- each level operation of the V-cycle of Algorithm 1 over the
+ * instances that have that level, the coarse GMRES with one CTA per instance
+ * -- replayed from a CUDA graph when opts->use_graph is set.  Per instance the
+ * method and its arithmetic are those of jfnk_solve.  stats (nullable) is an
+ * array of count entries.  Synchronises the stream. */
+jfnk_status jfnk_solve_batched(jfnk_problem* const* problems, int count, const jfnk_options* opts,
+                               double* const* u_inout, jfnk_stats* stats, void* stream);
+
 /* ---- building blocks of Algorithm 1, exposed one by one ---------------- */
 
 typedef enum {

@@ -239,6 +239,22 @@ class Problem:
             pass
 
 
+def solve_batched(problems, us, options=None, check=True):
+    """Lock-step batched JFNK-MG solve of independent 2D Bratu problems
+    (jfnk_solve_batched): one launch per level operation over all instances.
+    us[i] (FP64 full node grid of problem i) is updated in place.  Returns the
+    list of per-instance stats."""
+    n = len(problems)
+    o = options or problems[0].options
+    hs = (ctypes.c_void_p * n)(*[p._h.value for p in problems])
+    ups = (ctypes.c_void_p * n)(*[u.data_ptr() for u in us])
+    st = (_abi.Stats * n)()
+    status = lib().jfnk_solve_batched(hs, n, ctypes.byref(o), ups, st, _stream())
+    if check:
+        _check(status)
+    return [stats_dict(s) for s in st]
+
+
 def jvp_noalloc(kind, u, Fu, v, lam=0.0, kappa=None, load=None, eps=0.0, eps_mode=EPS_PAPER, out=None):
     """FD Jacobian action without a problem object or workspace (jfnk_jvp_noalloc),
     for callers that cannot allocate device memory; kappa and load must have u's

@@ -56,6 +56,8 @@ SIGNATURES = [
     ("jfnk_mg_setup", _i, [_vp, ctypes.POINTER(Options), _vp, _i, _vp]),
     ("jfnk_mg_vcycle", _i, [_vp, ctypes.POINTER(Options), _vp, _vp, _vp]),
     ("jfnk_solve", _i, [_vp, ctypes.POINTER(Options), _vp, ctypes.POINTER(Stats), _vp]),
+    ("jfnk_solve_batched", _i, [ctypes.POINTER(_vp), _i, ctypes.POINTER(Options), ctypes.POINTER(_vp),
+                                ctypes.POINTER(Stats), _vp]),
     ("jfnk_transfer", _i, [_vp, _i, _i, _i, _vp, _vp, _vp]),
     ("jfnk_smooth", _i, [_vp, ctypes.POINTER(Options), _i, _vp, _vp, _i, _i, _vp]),
     ("jfnk_coarse_solve", _i, [_vp, ctypes.POINTER(Options), _vp, _vp, _vp]),

@@ -138,8 +138,7 @@ __device__ __forceinline__ bool coarse_inner(const Grid& g, long long i) {
 }
 
 template <typename T, Prob P, bool ADJ>
-__global__ void __launch_bounds__(kCoarseThreads) coarse_gmres_kernel(CoarseArgs<T> a) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+__device__ void coarse_gmres_body(const CoarseArgs<T>& a, unsigned char* smem_raw) {
     const Grid g = a.g;
     const int N = (int)g.size;
     const int ne = (g.d == 3) ? g.n * g.n * g.n : g.n * g.n;
@@ -289,6 +288,20 @@ __global__ void __launch_bounds__(kCoarseThreads) coarse_gmres_kernel(CoarseArgs
     }
 }
 
+template <typename T, Prob P, bool ADJ>
+__global__ void __launch_bounds__(kCoarseThreads) coarse_gmres_kernel(CoarseArgs<T> a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    coarse_gmres_body<T, P, ADJ>(a, smem_raw);
+}
+
+// one CTA per instance of a batch (all instances share the coarse grid size)
+template <typename T, Prob P, bool ADJ>
+__global__ void __launch_bounds__(kCoarseThreads) coarse_gmres_batched_kernel(const CoarseArgs<T>* args) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const CoarseArgs<T> a = args[blockIdx.x];
+    coarse_gmres_body<T, P, ADJ>(a, smem_raw);
+}
+
 template <typename T>
 size_t coarse_smem_bytes(const Grid& g, int maxit) {
     const int ne = (g.d == 3) ? g.n * g.n * g.n : g.n * g.n;
@@ -338,5 +351,21 @@ jfnk_status launch_coarse(Prob prob, const CoarseArgs<T>& a, cudaStream_t st) {
 
 template jfnk_status launch_coarse<float>(Prob, const CoarseArgs<float>&, cudaStream_t);
 template jfnk_status launch_coarse<double>(Prob, const CoarseArgs<double>&, cudaStream_t);
+template <typename T>
+jfnk_status launch_coarse_batched(const CoarseArgs<T>& a0, const CoarseArgs<T>* dev_args, int count, cudaStream_t st) {
+    if (count <= 0) return JFNK_OK;
+    if (a0.g.size > JFNK_COARSE_MAX_NODES || a0.maxit > JFNK_COARSE_MAX_IT || a0.maxit < 1 || a0.g.d != 2) {
+        set_error("batched coarse solve: 2D coarse grids within the single-CTA limits only");
+        return JFNK_ERR_INVALID_ARG;
+    }
+    const size_t smem = coarse_smem_bytes<T>(a0.g, a0.maxit);
+    JFNK_CUDA_TRY(cudaFuncSetAttribute(coarse_gmres_batched_kernel<T, Prob::BRATU2, false>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    coarse_gmres_batched_kernel<T, Prob::BRATU2, false><<<count, kCoarseThreads, smem, st>>>(dev_args);
+    JFNK_LAUNCH_CHECK();
+    return JFNK_OK;
+}
+template jfnk_status launch_coarse_batched<float>(const CoarseArgs<float>&, const CoarseArgs<float>*, int, cudaStream_t);
+template jfnk_status launch_coarse_batched<double>(const CoarseArgs<double>&, const CoarseArgs<double>*, int, cudaStream_t);
 
 }  // namespace jfnk

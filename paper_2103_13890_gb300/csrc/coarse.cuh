@@ -28,5 +28,8 @@ struct CoarseArgs {
 
 template <typename T>
 jfnk_status launch_coarse(Prob prob, const CoarseArgs<T>& a, cudaStream_t st);
+// count instances (2D Bratu, same coarse grid as a0), args in device memory
+template <typename T>
+jfnk_status launch_coarse_batched(const CoarseArgs<T>& a0, const CoarseArgs<T>* dev_args, int count, cudaStream_t st);
 
 }  // namespace jfnk

@@ -35,15 +35,14 @@ __device__ __forceinline__ double block_sum(TA v, double* sm) {
     return t;
 }
 
-// Last-block completion.  Thread 0 of every block passes its block sum; returns
-// true in every thread of the last block, with the total in *total (thread 0).
-// The completion counter is reset by the last block.
-__device__ __forceinline__ bool grid_sum_last(double blocksum, double* partials, unsigned int* counter,
-                                              double* total, double* sm) {
+// Last-block completion over a segment of nb CTAs (bid = this CTA's index in
+// it).  Thread 0 of every block passes its block sum; returns true in every
+// thread of the last block of the segment, with the total in *total (thread
+// 0).  The completion counter is reset by the last block.
+__device__ __forceinline__ bool grid_sum_last_seg(double blocksum, double* partials, unsigned int* counter,
+                                                  double* total, double* sm, unsigned int bid, unsigned int nb) {
     const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
     const int nt = blockDim.x * blockDim.y * blockDim.z;
-    const unsigned int nb = gridDim.x * gridDim.y * gridDim.z;
-    const unsigned int bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
     __shared__ int s_last;
     if (tid == 0) {
         partials[bid] = blocksum;
@@ -62,6 +61,14 @@ __device__ __forceinline__ bool grid_sum_last(double blocksum, double* partials,
         *counter = 0u;
     }
     return true;
+}
+
+// The whole grid as one segment.
+__device__ __forceinline__ bool grid_sum_last(double blocksum, double* partials, unsigned int* counter,
+                                              double* total, double* sm) {
+    return grid_sum_last_seg(blocksum, partials, counter, total, sm,
+                             blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z),
+                             gridDim.x * gridDim.y * gridDim.z);
 }
 
 }  // namespace jfnk

@@ -16,6 +16,7 @@
 // coarse.cu; this file only sequences launches on one stream and reads back
 // the scalars that Newton and FGMRES branch on.
 #include <chrono>
+#include <map>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -28,6 +29,7 @@
 #include "stencil.cuh"
 #include "transfer.cuh"
 #include "vector.cuh"
+#include "batch.cuh"
 #include "profile.cuh"
 #include "stencil_v2.cuh"
 #include <algorithm>
@@ -98,6 +100,8 @@ struct jfnk_problem {
     void* coarseV;
     double* coarseH;
     double* mms_tab;
+    char* batch = nullptr;  // descriptor staging when this problem leads a batched solve
+    size_t batch_bytes = 0;
     char* face = nullptr;  // face buffer of the halo-free 3D kernel
     size_t face_bytes = 0;
     // captured V-cycle (Lf.b -> Lf.s) and the options it was captured for
@@ -203,6 +207,9 @@ static size_t plan(P& p, char* base, const jfnk_options* o) {
         const int cm = o->coarse_maxit > 0 ? o->coarse_maxit : (int)g0.interior();
         p.coarseV = pl.take<char>((size_t)(cm + 1) * g0.size * esz_pc);
         p.coarseH = pl.take<double>((size_t)(cm + 1) * cm);
+        // descriptor staging of batched solves led by this problem
+        p.batch_bytes = (size_t)32 << 20;
+        p.batch = pl.take<char>(p.batch_bytes);
     }
     return pl.off;
 }
@@ -1320,3 +1327,5 @@ jfnk_status jfnk_adjoint_solve(jfnk_problem* p, const jfnk_options* opts, const 
     if (p->pc == JFNK_F32) return adjoint_T<float>(*p, *opts, u, g, lambda, grad_kappa, rtol, stats, st);
     return adjoint_T<double>(*p, *opts, u, g, lambda, grad_kappa, rtol, stats, st);
 }
+
+#include "batch_solver.cuh"

@@ -1,0 +1,216 @@
+// Device building blocks shared by the element-residual kernels: FD-step and
+// Chebyshev-coefficient accessors, the per-node epilogues of the fused modes,
+// the norm reduction, and the 2D (Bratu) row-segment body used by both the
+// single-problem and the batched kernels.
+#pragma once
+#include "element.cuh"
+#include "reduce.cuh"
+#include "stencil.cuh"
+
+namespace jfnk {
+
+template <typename T>
+__device__ __forceinline__ T eps_of(const EpsSlot* s);
+template <>
+__device__ __forceinline__ double eps_of<double>(const EpsSlot* s) { return s->e; }
+template <>
+__device__ __forceinline__ float eps_of<float>(const EpsSlot* s) { return s->ef; }
+template <typename T>
+__device__ __forceinline__ T inv_eps_of(const EpsSlot* s);
+template <>
+__device__ __forceinline__ double inv_eps_of<double>(const EpsSlot* s) { return s->inv; }
+template <>
+__device__ __forceinline__ float inv_eps_of<float>(const EpsSlot* s) { return s->invf; }
+
+template <typename T>
+struct ChebK {
+    T theta_inv, c1, c2;
+};
+template <typename T>
+__device__ __forceinline__ ChebK<T> cheb_of(const ChebTable* t, int i);
+template <>
+__device__ __forceinline__ ChebK<double> cheb_of<double>(const ChebTable* t, int i) {
+    return {t->theta_inv, t->c1[i], t->c2[i]};
+}
+template <>
+__device__ __forceinline__ ChebK<float> cheb_of<float>(const ChebTable* t, int i) {
+    return {t->theta_invf, t->c1f[i], t->c2f[i]};
+}
+
+// Per-node epilogue.  val = A(w)_i (already scaled).  Boundary nodes get 0 in
+// every output.  `red` accumulates the square of the reduced quantity.
+template <typename T, Mode M>
+__device__ __forceinline__ void epilogue(const StencilArgs<T>& a, long long idx, bool inner, T val,
+                                         T inv_eps, const ChebK<T>& ck, float& red) {
+    if (M == Mode::F) {
+        T f = T(0), av = T(0);
+        if (inner) {
+            av = val;
+            f = val - (T)a.load_const;
+            if (a.load) f -= a.load[idx];
+        }
+        a.out[idx] = f;
+        if (a.out2) a.out2[idx] = av;
+        red += (float)f * (float)f;
+    } else if (M == Mode::JV) {
+        // Au may be F(u) = A(u) - load: the same load is then removed from A(w)
+        T jv = T(0);
+        if (inner) {
+            T aw = val - (T)a.load_const;
+            if (a.load) aw -= a.load[idx];
+            jv = (aw - a.Au[idx]) * inv_eps;
+        }
+        a.out[idx] = jv;
+        red += (float)jv * (float)jv;
+    } else if (M == Mode::BMJ) {
+        T o = inner ? a.rhs[idx] - (val - a.Au[idx]) * inv_eps : T(0);
+        a.out[idx] = o;
+        red += (float)o * (float)o;
+    } else if (M == Mode::CHEB0) {
+        T rr = T(0), dd = T(0);
+        if (inner) {
+            rr = a.rhs[idx] - (val - a.Au[idx]) * inv_eps;
+            dd = rr * ck.theta_inv;
+        }
+        a.out[idx] = rr;
+        a.out2[idx] = dd;
+        red += (float)dd * (float)dd;
+    } else if (M == Mode::CHEB) {
+        T rr = T(0), ss = T(0), dn = T(0);
+        if (inner) {
+            T jd = (val - a.Au[idx]) * inv_eps;
+            T dc = a.v[idx];
+            rr = a.r[idx] - jd;
+            ss = a.s[idx] + dc;
+            dn = ck.c1 * dc + ck.c2 * rr;
+        }
+        a.r[idx] = rr;
+        a.s[idx] = ss;
+        a.dnew[idx] = dn;
+        red += (float)dn * (float)dn;
+    } else {  // CHEBLAST
+        T ss = T(0);
+        if (inner) {
+            T jd = (val - a.Au[idx]) * inv_eps;
+            T dc = a.v[idx];
+            T rr = a.r[idx] - jd;
+            T dn = ck.c1 * dc + ck.c2 * rr;
+            ss = a.s[idx] + dc + dn;
+        }
+        a.s[idx] = ss;
+        red += (float)ss * (float)ss;
+    }
+}
+
+// bid / nb: index of this CTA among the nb CTAs that reduce together (the
+// whole grid, or one instance's CTAs in a batched launch)
+template <typename T>
+__device__ __forceinline__ void stencil_reduce(const StencilArgs<T>& a, float red, double* sm, unsigned int bid,
+                                               unsigned int nb) {
+    if (a.red == RedOut::NONE) return;
+    double bs = block_sum(red, sm);
+    double tot = 0.0;
+    if (grid_sum_last_seg(bs, a.partials, a.counter, &tot, sm, bid, nb)) {
+        if (threadIdx.x == 0 && threadIdx.y == 0) {
+            double nrm = sqrt(tot);
+            if (a.red_norm) *a.red_norm = nrm;
+            if (a.red == RedOut::EPS) {
+                double e = eps_formula(a.epsp.mode, a.epsp.n_unknowns, *a.epsp.xstat, nrm);
+                double inv = e > 0.0 ? 1.0 / e : 0.0;
+                if (!isfinite(e) || !isfinite(inv)) {
+                    if (a.status) atomicOr(a.status, 1);
+                    e = 0.0;
+                    inv = 0.0;
+                }
+                a.red_eps->e = e;
+                a.red_eps->inv = inv;
+                a.red_eps->ef = (float)e;
+                a.red_eps->invf = (float)inv;
+            }
+        }
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ void stencil_reduce(const StencilArgs<T>& a, float red, double* sm) {
+    stencil_reduce(a, red, sm, blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z),
+                   gridDim.x * gridDim.y * gridDim.z);
+}
+
+// ---------------------------------------------------------------------------
+// 2D kernel (Bratu), blockDim.x = BX threads, BX-1 output nodes per row segment
+// ---------------------------------------------------------------------------
+// Row segment [x0, x0+txo) of node rows [y0, y1): blockDim.x = BX >= txo + 1
+// threads; smem_raw holds sizeof(T) * (2 (BX+1) + 4 BX) bytes.
+template <typename T, Mode M>
+__device__ __forceinline__ void stencil2d_body(const StencilArgs<T>& a, int x0, int y0, int y1, int txo,
+                                               unsigned int red_bid, unsigned int red_nb, unsigned char* smem_raw,
+                                               double* red_sm) {
+    const int BX = blockDim.x;
+    T* W = reinterpret_cast<T*>(smem_raw);  // [2][BX + 1]
+    T* C = W + 2 * (BX + 1);                // [4][BX]
+    const int tx = threadIdx.x;
+    const Grid g = a.g;
+    const int n = g.n;
+    T eps = T(0), inv_eps = T(0);
+    if (M != Mode::F) {
+        eps = eps_of<T>(a.eps);
+        inv_eps = inv_eps_of<T>(a.eps);
+    }
+    ChebK<T> ck = {T(0), T(0), T(0)};
+    if (M == Mode::CHEB0 || M == Mode::CHEB || M == Mode::CHEBLAST) ck = cheb_of<T>(a.cheb, a.cheb_step);
+    const int ex = x0 - 1 + tx;
+    const bool elem_x = tx <= txo && ex >= 0 && ex < n;
+    const int nx_o = x0 + tx;
+    const bool node_thr = tx < txo && nx_o < g.nx;
+    const bool inner_x = nx_o > 0 && nx_o < g.nx - 1;
+
+    auto load_row = [&](int y, int buf) {
+        for (int i = tx; i < txo + 2; i += BX) {
+            const int x = x0 - 1 + i;
+            T val = T(0);
+            if (x >= 0 && x < g.nx && y >= 0 && y < g.ny) {
+                const long long idx = (long long)y * g.sy + x;
+                val = a.u[idx];
+                if (M != Mode::F) {
+                    const bool bnd = x == 0 || x == g.nx - 1 || y == 0 || y == g.ny - 1;
+                    if (!bnd) val += eps * a.v[idx];
+                }
+            }
+            W[buf * (BX + 1) + i] = val;
+        }
+    };
+
+    T carry = T(0);
+    float red = 0.f;
+    load_row(y0 - 1, (y0 - 1) & 1);
+    for (int j = y0 - 1; j < y1; ++j) {
+        load_row(j + 1, (j + 1) & 1);
+        __syncthreads();
+        T r[4];
+        if (elem_x && j >= 0 && j < n) {
+            const T* w0 = W + (j & 1) * (BX + 1);
+            const T* w1 = W + ((j + 1) & 1) * (BX + 1);
+            T ue[4] = {w0[tx], w0[tx + 1], w1[tx], w1[tx + 1]};
+            elem_bratu2<T>(ue, a.lh, r);
+        } else {
+            r[0] = r[1] = r[2] = r[3] = T(0);
+        }
+#pragma unroll
+        for (int c = 0; c < 4; ++c) C[c * BX + tx] = r[c];
+        __syncthreads();
+        if (node_thr) {
+            const T lower = C[1 * BX + tx] + C[0 * BX + tx + 1];
+            const T upper = C[3 * BX + tx] + C[2 * BX + tx + 1];
+            if (j >= y0) {
+                const long long idx = (long long)j * g.sy + nx_o;
+                const bool inner = inner_x && j > 0 && j < g.ny - 1;
+                epilogue<T, M>(a, idx, inner, (carry + lower) * a.node_scale, inv_eps, ck, red);
+            }
+            carry = upper;
+        }
+    }
+    stencil_reduce(a, red, red_sm, red_bid, red_nb);
+}
+
+}  // namespace jfnk

@@ -120,6 +120,66 @@ __device__ __forceinline__ void epilogue2(const StencilArgs<T>& a, long long idx
     }
 }
 
+// Epilogue operands of one node, loaded at the start of a layer so that their
+// latency overlaps the element arithmetic.
+template <typename T>
+struct EpiIn {
+    T au, vv, rr, ss, rhs, ld;
+};
+
+template <typename T, Mode M>
+__device__ __forceinline__ void epi_load(const StencilArgs<T>& a, long long idx, EpiIn<T>& e) {
+    if (M == Mode::F || M == Mode::JV) e.ld = a.load ? a.load[idx] : T(0);
+    if (M != Mode::F) e.au = a.Au[idx];
+    if (M == Mode::BMJ || M == Mode::CHEB0) e.rhs = a.rhs[idx];
+    if (M == Mode::CHEB || M == Mode::CHEBLAST) {
+        e.vv = a.v[idx];
+        e.rr = a.r[idx];
+        e.ss = a.s[idx];
+    }
+}
+
+// Same definitions as epilogue2 for an interior node, operands from e.
+template <typename T, Mode M>
+__device__ __forceinline__ void epilogue2_pf(const StencilArgs<T>& a, long long idx, T val, T inv_eps,
+                                             const ChebK2<T>& ck, const EpiIn<T>& e, float& red) {
+    if (M == Mode::F) {
+        const T f = val - (T)a.load_const - e.ld;
+        a.out[idx] = f;
+        if (a.out2) a.out2[idx] = val;
+        red += (float)f * (float)f;
+    } else if (M == Mode::JV) {
+        const T jv = (val - (T)a.load_const - e.ld - e.au) * inv_eps;
+        a.out[idx] = jv;
+        red += (float)jv * (float)jv;
+    } else if (M == Mode::BMJ) {
+        const T o = e.rhs - (val - e.au) * inv_eps;
+        a.out[idx] = o;
+        red += (float)o * (float)o;
+    } else if (M == Mode::CHEB0) {
+        const T rr = e.rhs - (val - e.au) * inv_eps;
+        const T dd = rr * ck.theta_inv;
+        a.out[idx] = rr;
+        a.out2[idx] = dd;
+        red += (float)dd * (float)dd;
+    } else if (M == Mode::CHEB) {
+        const T jd = (val - e.au) * inv_eps;
+        const T rr = e.rr - jd;
+        const T dn = ck.c1 * e.vv + ck.c2 * rr;
+        a.r[idx] = rr;
+        a.s[idx] = e.ss + e.vv;
+        a.dnew[idx] = dn;
+        red += (float)dn * (float)dn;
+    } else {
+        const T jd = (val - e.au) * inv_eps;
+        const T rr = e.rr - jd;
+        const T dn = ck.c1 * e.vv + ck.c2 * rr;
+        const T ss = e.ss + e.vv + dn;
+        a.s[idx] = ss;
+        red += (float)ss * (float)ss;
+    }
+}
+
 // Face buffer addressing
 __device__ __forceinline__ long long ylo_idx(const V2Geom& q, int ty, int c, int zl, int x) {
     return q.ylo + (((long long)ty * q.Tz + c) * (q.ZC + 1) + zl) * (q.n + 1) + x;
@@ -139,7 +199,7 @@ __global__ void __launch_bounds__(kV2Threads, 1) stencil3d_v2_kernel(const Stenc
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int n = q.n, BY = q.BY, NP = n + 1;
     T* W = reinterpret_cast<T*>(smem_raw);  // [3][BY+1][n+1]
-    T* C = W + 3 * (BY + 1) * NP;           // [8][BY][n]
+    T* C2 = W + 3 * (BY + 1) * NP;          // [2][8][BY][n] (double-buffered by layer parity)
     __shared__ double red_sm[32];
     const Grid g = a.g;
     const int tx = threadIdx.x, w = threadIdx.y;
@@ -202,8 +262,14 @@ __global__ void __launch_bounds__(kV2Threads, 1) stencil3d_v2_kernel(const Stenc
     const ChebK2<T> ck0 = ck;
 
     for (int k = z0; k < z1; ++k) {
+        T* C = C2 + (k & 1) * 8 * BY * n;
         const bool pf = (k + 2 <= z1);
         if (pf) load4(k + 2, q0, q1, q2, q3);
+        // operands of the node epilogue of this layer (complete nodes only)
+        const long long idxA = (long long)k * g.sz + (long long)yA * g.sy + tx;
+        const bool completeA = !(k == 0 || bndA || tx == 0 || faceA || k == z0);
+        EpiIn<T> eA;
+        if (completeA) epi_load<T, M>(a, idxA, eA);
         const T* W0 = W + (k % 3) * (BY + 1) * NP;
         const T* W1 = W + ((k + 1) % 3) * (BY + 1) * NP;
         T ue[8] = {W0[w * NP + tx],       W0[w * NP + tx + 1],       W0[(w + 1) * NP + tx],
@@ -216,6 +282,9 @@ __global__ void __launch_bounds__(kV2Threads, 1) stencil3d_v2_kernel(const Stenc
             elem_nd3<T, false>(ue, T(1), r);
 #pragma unroll
         for (int cc = 0; cc < 8; ++cc) C[(cc * BY + w) * n + tx] = r[cc];
+        // the ring slot of plane k+2 was last read by layer k-1 (before the
+        // previous barrier); the barrier below publishes it for layer k+1
+        if (pf) store4((k + 2) % 3, q0, q1, q2, q3);
         __syncthreads();
         // own row y0+w: b = 0 corners of row w, b = 1 corners of row w-1
         T loA = C[(0 * BY + w) * n + tx];
@@ -252,7 +321,7 @@ __global__ void __launch_bounds__(kV2Threads, 1) stencil3d_v2_kernel(const Stenc
             } else if (k == z0) {
                 a.face[zlo_idx(q, ty, c, w, tx)] = vA;
             } else {
-                epilogue2<T, M>(a, idx, true, vA * scale, inv_eps, ck0, red);
+                epilogue2_pf<T, M>(a, idx, vA * scale, inv_eps, ck0, eA, red);
             }
             if (extra_col) epilogue2<T, M>(a, idx + 1, false, zero, inv_eps, ck0, red);  // x = n
             carryA = hiA;
@@ -268,9 +337,6 @@ __global__ void __launch_bounds__(kV2Threads, 1) stencil3d_v2_kernel(const Stenc
             if (extra_col) epilogue2<T, M>(a, idx + 1, false, zero, inv_eps, ck0, red);
             carryB = hiB;
         }
-        __syncthreads();
-        if (pf) store4((k + 2) % 3, q0, q1, q2, q3);
-        __syncthreads();
     }
     // plane z1: the carries are partial sums from the last layer only
     {
@@ -446,11 +512,11 @@ static jfnk_status launch_v2_pm(const StencilArgs<T>& a, cudaStream_t st) {
         set_error("v2 grid too large for the reduction scratch");
         return JFNK_ERR_INVALID_ARG;
     }
-    const size_t smem = sizeof(T) * (3 * (size_t)(q.BY + 1) * (q.n + 1) + 8 * (size_t)q.BY * q.n);
+    const size_t smem = sizeof(T) * (3 * (size_t)(q.BY + 1) * (q.n + 1) + 16 * (size_t)q.BY * q.n);
     static bool attr_set = false;
     if (!attr_set) {
         JFNK_CUDA_TRY(cudaFuncSetAttribute(stencil3d_v2_kernel<T, P, M>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           200 * 1024));
+                                           220 * 1024));
         attr_set = true;
     }
     stencil3d_v2_kernel<T, P, M><<<dim3(q.Ty, q.Tz), dim3(q.n, q.BY), smem, st>>>(a, q);

@@ -1,0 +1,63 @@
+"""GPU tests of the batched solve of independent 2D Bratu instances of uneven
+sizes (one launch per level operation across the instances): every instance
+must reach the same discrete solution as its own single-problem solve and as
+the oracle's exact-Newton solve."""
+import numpy as np
+import pytest
+
+from gpu_common import host, jf, rel, torch
+from oracle import adjoint
+from workloads import batch_instances
+
+pytestmark = pytest.mark.gpu
+
+
+def _opts(pc="f32", rtol=1e-10, graph=1):
+    m = jf()
+    return m.default_options(rtol_newton=rtol, pc_dtype=m.F32 if pc == "f32" else m.F64,
+                             eps_mode_pc=m.EPS_FP32 if pc == "f32" else m.EPS_PAPER, use_graph=graph)
+
+
+def _levels(n, coarse=8):
+    return int(np.log2(n // coarse)) + 1
+
+
+@pytest.mark.parametrize("pc,graph", [("f64", 0), ("f32", 1), ("f64", 1)])
+def test_batch_matches_single_and_exact_solutions(pc, graph):
+    specs = [(32, 5.0), (64, 2.0), (16, 6.3), (64, 4.4), (32, 1.0), (128, 3.3)]
+    o = _opts(pc, graph=graph)
+    ps = [jf().Problem("bratu2d", n, _levels(n), lam=lam, options=o) for n, lam in specs]
+    us = [torch.zeros((n + 1, n + 1), dtype=torch.float64, device="cuda") for n, _ in specs]
+    stats = jf().solve_batched(ps, us, o)
+    for (n, lam), u, st, p in zip(specs, us, stats, ps):
+        assert st["converged"], st
+        # the same instance solved alone
+        us1 = torch.zeros_like(u)
+        q = jf().Problem("bratu2d", n, _levels(n), lam=lam, options=o)
+        st1 = q.solve(us1)
+        assert rel(host(u), host(us1)) <= 1e-9
+        assert st["newton_its"] == st1["newton_its"]
+        if n <= 64:
+            ud, _ = adjoint.newton_direct("bratu2d", np.zeros((n + 1, n + 1)), lam=lam)
+            assert rel(host(u), ud) <= 1e-8
+
+
+def test_batch_of_64_uneven_instances():
+    """The configured batch: 64 instances, sizes from {129^2, 257^2, 513^2} nodes,
+    lambda ~ U[1, 6.5] (seeded), FP32 preconditioner, FP64 outer, 1e-8."""
+    inst = batch_instances(64, seed=4)
+    o = _opts("f32", rtol=1e-8)
+    ps = [jf().Problem("bratu2d", n, _levels(n), lam=lam, options=o) for n, lam in inst]
+    us = [torch.zeros((n + 1, n + 1), dtype=torch.float64, device="cuda") for n, _ in inst]
+    stats = jf().solve_batched(ps, us, o)
+    assert all(s["converged"] for s in stats)
+    # spot-check three instances of different sizes against single solves
+    seen = {}
+    for k, (n, lam) in enumerate(inst):
+        if n not in seen:
+            seen[n] = k
+    for n, k in seen.items():
+        q = jf().Problem("bratu2d", n, _levels(n), lam=inst[k][1], options=o)
+        u1 = torch.zeros_like(us[k])
+        q.solve(u1)
+        assert rel(host(us[k]), host(u1)) <= 1e-6
