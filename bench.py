@@ -13,8 +13,12 @@ e2e:     the same through the C ABI with the initial guess copied from pinned
 extras:  FP32-preconditioned solve of the same workload (FP32 vs FP64 PC) and
          residual-evaluation DOF/s with %HBM.
 roofline: the dominant kernel (the FP64 element-residual kernel with the fused
-         Chebyshev epilogue) timed with CUDA events on its stream during the timed
-         solves; FP64-ALU bound.
+         Chebyshev epilogue) timed with CUDA events on its stream during K more
+         solves right after the timed ones (the value itself is timed without
+         per-launch events, V-cycles replayed from their CUDA graph); FP64-ALU
+         bound.
+extras:  also the 64-instance batched Bratu solve vs the same instances one by
+         one, and the forward + adjoint solve of the coefficient problem.
 cpu_baseline / --impl reference: the CPU oracle timed on a bounded sample.
 
 Multi-GPU (torchrun, N > 1): replicas only -- every rank solves its own
@@ -287,7 +291,6 @@ def main():
         dist.barrier()
     torch.cuda.synchronize()
     jf.kernel_launches(reset=True)
-    jf.profile_enable(True)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     stats = []
@@ -296,8 +299,6 @@ def main():
     e1.record(stream)
     torch.cuda.synchronize()
     launches = jf.kernel_launches()
-    prof = jf.profile_read()
-    jf.profile_enable(False)
     ms = e0.elapsed_time(e1) / args.steps
     if dist:
         t = torch.tensor([ms], device="cuda")
@@ -305,6 +306,20 @@ def main():
         ms = float(t.item())
         dist.barrier()
     clocks = sampler.stop()
+
+    # ---- the same K solves with every element-kernel launch bracketed by CUDA
+    # events on its stream (V-cycles then launch directly instead of through
+    # their graph): per-kernel durations for the roofline ----------------------
+    jf.profile_enable(True)
+    e0p, e1p = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0p.record(stream)
+    for _ in range(args.steps):
+        solve_once(p64)
+    e1p.record(stream)
+    torch.cuda.synchronize()
+    prof = jf.profile_read()
+    jf.profile_enable(False)
+    ms_prof = e0p.elapsed_time(e1p) / args.steps
 
     # ---- e2e through the C ABI with host buffers -----------------------------
     u_host = torch.zeros(shape, dtype=torch.float64).pin_memory()
@@ -377,8 +392,10 @@ def main():
         total_ms_all = sum(v[1] for v in prof.values())
         roof = {"kernel": name, "bound": "alu", "achieved": achieved, "peak": peak,
                 "unit": "Top/s (fp64 pipe)", "frac": achieved / peak, "traffic": None,
-                "avg_launch_ms": avg_s * 1e3, "launches_in_timed_region": cnt,
+                "avg_launch_ms": avg_s * 1e3, "launches": cnt,
                 "share_of_stencil_time": tot / total_ms_all if total_ms_all else None,
+                "timed_region": f"{args.steps} event-bracketed solves after the value's timed region "
+                                f"({ms_prof:.1f} ms per solve)",
                 "peak_source": "measured fp64 pipe rate of this pool's GB300 (bench docstring)"}
 
     cpu = None

@@ -42,6 +42,30 @@ Readings (the paper is silent or differs from the configured workloads):
   * P x^(k) and F(P x^(k)) on each level are evaluated once per Newton step
     (x^(k) does not change during the step, so this equals re-evaluating
     them inside every cycle as Alg. 1 writes it).
+
+The paper's own solver variant (``paper_options``): CG outer Krylov method,
+coarse CG preconditioned by L-BFGS with the spectral shift of Alg. 1.  Its
+readings:
+  * "V(5,5)" = one application of the degree-5 Chebyshev polynomial per side
+    (one recurrence step per smoothing step).
+  * Outer CG, negative curvature p.Jp <= 0: stop and return the current
+    iterate, or the first search direction when it happens at the first
+    iteration (Nocedal & Wright, Numerical Optimization, 2nd ed., Alg. 7.1).
+  * Coarse CG: stop at ||r|| <= tol ||b|| (relative reading, as for GMRES) or
+    after n_0 iterations per call; on negative curvature return the current
+    iterate and lambda_c = p.A_s p / p.p of the operator CG is applied to,
+    A_s = A - lambda_c+ I (lambda_c+ <= 0); a call without negative curvature
+    returns lambda_c = 0.  A shifted call restarts CG from the returned s_0.
+  * Secant pairs (Morales & Nocedal, SIAM J. Optim. 10 (2000)): during the very
+    first coarse CG call every step gives s_i = alpha_i p_i, y_i = alpha_i A p_i;
+    after that call m of the k pairs are kept, those of iterations
+    floor(j k / m), j = 0..m-1 (all of them when k <= m) -- "uniform sampling".
+    The preconditioner is the L-BFGS inverse-Hessian approximation applied by
+    the two-loop recursion (Nocedal & Wright, Alg. 7.4) with
+    H_0 = (s^T y / y^T y) I of the last kept pair; it is kept for the rest of
+    the solve.
+  * At most 30 shifted calls per coarse solve (the shift grows at least by the
+    factor gamma per call).
 """
 from dataclasses import dataclass, field
 
@@ -77,6 +101,23 @@ class Options:
     line_search: bool = True
     ls_max: int = 10
     seed: int = 0
+    outer: str = "fgmres"           # or "cg" (the paper's outer method)
+    coarse: str = "gmres"           # or "cgqn" (the paper's coarse solver)
+    lbfgs_pairs: int = 20
+    shift_gamma: float = 5.0
+
+
+def paper_options(**kw):
+    """The paper's own settings (Sec. 2 and Sec. 3 "Setup"): CG preconditioned by
+    the V(5,5) cycle, Chebyshev on [0.06, 1.2] lambda_l, power method to 30
+    iterations or a change below 1e-2, coarse CG with 20 L-BFGS secant pairs and
+    the spectral shift gamma = 5, eta = min(0.5, ||F||), stop at ||F|| < 1e-6."""
+    o = Options(nu_pre=1, nu_post=1, cheb_degree=5, cheb_lo=0.06, cheb_hi=1.2, power_iters=30,
+                power_tol=1e-2, rtol_newton=0.0, atol_newton=1e-6, eta_mode="paper", outer="cg",
+                coarse="cgqn", lbfgs_pairs=20, shift_gamma=5.0)
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
 
 
 # ---------------------------------------------------------------------------
@@ -99,6 +140,7 @@ class Level:
         self.Fx = None
         self.lam_max = None
         self.power_v = None
+        self.lbfgs = None    # coarse level: L-BFGS preconditioner of the first coarse CG call
 
     def F(self, x):
         self.ge += 1
@@ -291,6 +333,145 @@ def gmres(apply_A, b, mask, tol, maxit, precond=None, restart=None, tol_abs=None
 
 
 # ---------------------------------------------------------------------------
+# Conjugate gradients, L-BFGS preconditioner, shifted coarse CG
+# (Sec. 2 "The coarse level solver", Alg. 1, Sec. 3 "Setup")
+# ---------------------------------------------------------------------------
+
+def _dot(a, b, mask):
+    return float(np.sum(a[mask] * b[mask]))
+
+
+def pcg(apply_A, b, mask, tol, maxit, precond=None, tol_abs=None):
+    """Preconditioned CG for A x = b from x0 = 0 (the paper's outer Krylov method).
+    Stops at ||r|| <= tol ||b|| (or tol_abs) or after maxit iterations.  On
+    negative curvature p.Ap <= 0 it stops and returns the current iterate, or
+    the first search direction if that happens at the first iteration.
+    Returns (x, iterations, ||r||, negative_curvature)."""
+    x = np.zeros_like(b)
+    r = np.where(mask, b, 0.0)
+    res = norm_i(r, mask)
+    target = tol_abs if tol_abs is not None else tol * res
+    if res == 0.0 or res <= target:
+        return x, 0, res, False
+    z = np.where(mask, r if precond is None else precond(r), 0.0)
+    p = z
+    rz = _dot(r, z, mask)
+    for it in range(1, maxit + 1):
+        q = np.where(mask, apply_A(p), 0.0)
+        pq = _dot(p, q, mask)
+        if pq <= 0.0:
+            return (p if it == 1 else x), it, res, True
+        alpha = rz / pq
+        x = x + alpha * p
+        r = r - alpha * q
+        res = norm_i(r, mask)
+        if res <= target:
+            return x, it, res, False
+        z = np.where(mask, r if precond is None else precond(r), 0.0)
+        rz_new = _dot(r, z, mask)
+        p = z + (rz_new / rz) * p
+        rz = rz_new
+    return x, maxit, res, False
+
+
+class LBFGS:
+    """L-BFGS inverse-Hessian approximation H from secant pairs (s_i, y_i), oldest
+    first, applied by the two-loop recursion (Nocedal & Wright, Alg. 7.4) with
+    H_0 = gamma I, gamma = s^T y / y^T y of the last pair."""
+
+    def __init__(self, pairs, mask):
+        self.S = [p[0] for p in pairs]
+        self.Y = [p[1] for p in pairs]
+        self.mask = mask
+
+    def apply(self, r):
+        m = self.mask
+        q = np.where(m, r, 0.0)
+        k = len(self.S)
+        if k == 0:
+            return q
+        rho = [1.0 / _dot(self.Y[i], self.S[i], m) for i in range(k)]
+        a = [0.0] * k
+        for i in range(k - 1, -1, -1):
+            a[i] = rho[i] * _dot(self.S[i], q, m)
+            q = q - a[i] * self.Y[i]
+        gamma = _dot(self.S[-1], self.Y[-1], m) / _dot(self.Y[-1], self.Y[-1], m)
+        z = gamma * q
+        for i in range(k):
+            bta = rho[i] * _dot(self.Y[i], z, m)
+            z = z + (a[i] - bta) * self.S[i]
+        return z
+
+
+def uniform_sample(pairs, m):
+    """Keep the pairs of iterations floor(j k / m), j = 0..m-1, of a run of k steps
+    (all of them when k <= m)."""
+    k = len(pairs)
+    if k <= m:
+        return list(pairs)
+    return [pairs[(j * k) // m] for j in range(m)]
+
+
+def coarse_cg(apply_A, b, mask, s0, shift, tol, maxit, H=None, collect=None, tol_abs=None):
+    """CG(s_0, x_0, F(x_0), r_0, lambda_c+, nu_*) of Alg. 1: CG for
+    (A - lambda_c+ I) s = b from s_0, preconditioned by the L-BFGS operator H when
+    given.  Appends the secant pairs (alpha p, alpha A_s p) to ``collect`` when
+    it is a list.  Returns (s, lambda_c, iterations): lambda_c is the Rayleigh
+    quotient p.A_s p / p.p at negative curvature, else 0."""
+    def A_s(v):
+        return np.where(mask, apply_A(v) - shift * v, 0.0)
+
+    x = np.where(mask, s0, 0.0)
+    nb = norm_i(b, mask)
+    target = tol_abs if tol_abs is not None else tol * nb
+    r = np.where(mask, b, 0.0) - (A_s(x) if np.any(x[mask] != 0.0) else 0.0)
+    res = norm_i(r, mask)
+    if res == 0.0 or res <= target:
+        return x, 0.0, 0
+    z = H.apply(r) if H is not None else r
+    p = z
+    rz = _dot(r, z, mask)
+    for it in range(1, maxit + 1):
+        q = A_s(p)
+        pq = _dot(p, q, mask)
+        if pq <= 0.0:
+            return x, pq / _dot(p, p, mask), it
+        alpha = rz / pq
+        if collect is not None:
+            collect.append((alpha * p, alpha * q))
+        x = x + alpha * p
+        r = r - alpha * q
+        res = norm_i(r, mask)
+        if res <= target:
+            return x, 0.0, it
+        z = H.apply(r) if H is not None else r
+        rz_new = _dot(r, z, mask)
+        p = z + (rz_new / rz) * p
+        rz = rz_new
+    return x, 0.0, maxit
+
+
+def coarse_cgqn(apply_A, b, lv, tol, maxit, m, gamma, tol_abs=None, max_shifts=30):
+    """Coarse branch of Alg. 1: lambda_c+ = 0; (s_0, lambda_c) = CG(...); while
+    lambda_c < 0: lambda_c+ = gamma min(lambda_c, lambda_c+), (s_0, lambda_c) =
+    CG(...) with the shifted operator.  The first call on this level collects the
+    secant pairs of the L-BFGS preconditioner (kept in lv.lbfgs).
+    Returns (s_0, list of the shifts lambda_c+ used)."""
+    shift = 0.0
+    collect = [] if lv.lbfgs is None else None
+    s, lam_c, _ = coarse_cg(apply_A, b, lv.mask, np.zeros_like(b), shift, tol, maxit, lv.lbfgs, collect,
+                            tol_abs)
+    if collect is not None:
+        lv.lbfgs = LBFGS(uniform_sample(collect, m), lv.mask)
+    shifts = [shift]
+    while lam_c < 0.0 and len(shifts) <= max_shifts:
+        shift = gamma * min(lam_c, shift)
+        shifts.append(shift)
+        s, lam_c, _ = coarse_cg(apply_A, b, lv.mask, s, shift, tol, maxit, lv.lbfgs, None, tol_abs)
+    return s, shifts
+
+
+# ---------------------------------------------------------------------------
 # Algorithm 1: Jacobian-free multigrid V(nu1, nu2)-cycle
 # ---------------------------------------------------------------------------
 
@@ -312,8 +493,12 @@ def mg_vcycle(levels, l, b, opts):
     else:
         maxit = opts.coarse_maxit if opts.coarse_maxit > 0 else lv.n_unknowns
         tol_abs = opts.coarse_tol if opts.coarse_tol_mode == "absolute" else None
-        s, _, _ = gmres(lambda v: fd_jv(lv, lv.x, lv.Fx, v, mode), b, lv.mask,
-                        opts.coarse_tol, maxit, tol_abs=tol_abs)
+        apply_A = lambda v: fd_jv(lv, lv.x, lv.Fx, v, mode)  # noqa: E731
+        if opts.coarse == "cgqn":
+            s, _ = coarse_cgqn(apply_A, b, lv, opts.coarse_tol, maxit, opts.lbfgs_pairs,
+                               opts.shift_gamma, tol_abs=tol_abs)
+        else:
+            s, _, _ = gmres(apply_A, b, lv.mask, opts.coarse_tol, maxit, tol_abs=tol_abs)
     return s
 
 
@@ -385,7 +570,8 @@ class Stats:
 
 def newton_solve(levels, u0, opts):
     """Inexact JFNK: x^(k+1) = x^(k) + alpha dx^(k), J dx = -F by MG-preconditioned
-    FGMRES to ||J dx + F|| <= eta ||F||.  Returns (u, Stats)."""
+    FGMRES (or CG, the paper's choice) to ||J dx + F|| <= eta ||F||.
+    Returns (u, Stats)."""
     L = len(levels) - 1
     fine = levels[L]
     st = Stats()
@@ -405,9 +591,13 @@ def newton_solve(levels, u0, opts):
         else:
             eta = min(opts.eta_max, normF / F0)
         Fx = F
-        du, its, _ = gmres(lambda v: fd_jv(fine, u, Fx, v, "paper"), -F, fine.mask, eta,
-                           opts.max_linear, precond=lambda v: mg_vcycle(levels, L, v, opts),
-                           restart=opts.restart)
+        apply_J = lambda v: fd_jv(fine, u, Fx, v, "paper")  # noqa: E731
+        mg = lambda v: mg_vcycle(levels, L, v, opts)  # noqa: E731
+        if opts.outer == "cg":
+            du, its, _, _ = pcg(apply_J, -F, fine.mask, eta, opts.max_linear, precond=mg)
+        else:
+            du, its, _ = gmres(apply_J, -F, fine.mask, eta, opts.max_linear, precond=mg,
+                               restart=opts.restart)
         st.linear_its += its
         st.lin_hist.append(its)
         if opts.line_search:

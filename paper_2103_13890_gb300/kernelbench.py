@@ -3,9 +3,13 @@
     python -m paper_2103_13890_gb300.kernelbench --kind nd3d --n 160 --op smooth --dtype f64
 
 op: residual | jvp | smooth (one Chebyshev application = start + fused steps)
-    | vcycle.  Prints one JSON line with the mean time per call (CUDA events on
-the current stream, after warm-up) and, for the element kernels, the achieved
-FP64/FP32 operation rate and HBM bandwidth of the algorithmic traffic.
+    | vcycle | solve (a whole JFNK-MG solve from u0 = 0 to 1e-8, preconditioner
+    in --dtype).  Prints one JSON line with the mean time per call (CUDA events
+on the current stream, after warm-up) and, for the element kernels, the
+achieved FP64/FP32 operation rate and HBM bandwidth of the algorithmic traffic.
+
+--profiler-range brackets the timed calls with cudaProfilerStart/Stop, so that a
+profiler started with profiling off captures exactly those launches.
 """
 import argparse
 import json
@@ -22,10 +26,12 @@ def main():
     ap.add_argument("--kind", default="nd3d", choices=list(OPS_PER_ELEMENT))
     ap.add_argument("--n", type=int, default=128)
     ap.add_argument("--levels", type=int, default=0, help="0: coarsest level with 4 elements")
-    ap.add_argument("--op", default="residual", choices=["residual", "jvp", "smooth", "vcycle"])
+    ap.add_argument("--op", default="residual", choices=["residual", "jvp", "smooth", "vcycle", "solve"])
     ap.add_argument("--dtype", default="f64", choices=["f64", "f32"])
     ap.add_argument("--reps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--rtol", type=float, default=1e-8)
+    ap.add_argument("--profiler-range", action="store_true")
     a = ap.parse_args()
     d = 2 if a.kind == "bratu2d" else 3
     n = a.n
@@ -37,7 +43,7 @@ def main():
     dt = torch.float64 if a.dtype == "f64" else torch.float32
     o = jf.default_options(pc_dtype=jf.F64 if a.dtype == "f64" else jf.F32,
                            eps_mode_pc=jf.EPS_PAPER if a.dtype == "f64" else jf.EPS_FP32,
-                           nu_pre=2, nu_post=2, cheb_degree=4)
+                           nu_pre=2, nu_post=2, cheb_degree=4, rtol_newton=a.rtol)
     kappa = None
     if a.kind == "ndk3d":
         g = torch.Generator().manual_seed(0)
@@ -58,6 +64,8 @@ def main():
     F = p.residual(uT)
     out = torch.empty_like(uT)
     s = torch.zeros_like(uT)
+    out64 = torch.empty_like(u)
+    usol = torch.zeros_like(u)
 
     def call():
         if a.op == "residual":
@@ -67,18 +75,25 @@ def main():
         elif a.op == "smooth":
             s.zero_()
             p.smooth(vT, s, level=levels - 1, nu=1, s_is_zero=True)
+        elif a.op == "vcycle":
+            p.mg_vcycle(v, out=out64)
         else:
-            p.mg_vcycle(v, out=out.double() if a.dtype == "f32" else out)
+            usol.zero_()
+            return p.solve(usol)
 
     for _ in range(a.warmup):
         call()
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if a.profiler_range:
+        torch.cuda.profiler.start()
     e0.record()
     for _ in range(a.reps):
-        call()
+        st = call()
     e1.record()
     torch.cuda.synchronize()
+    if a.profiler_range:
+        torch.cuda.profiler.stop()
     ms = e0.elapsed_time(e1) / a.reps
     elems = n ** d
     w = 8 if a.dtype == "f64" else 4
@@ -86,6 +101,8 @@ def main():
     stencils = {"residual": 1, "jvp": 1, "smooth": o.cheb_degree - 1}.get(a.op)
     words = {"residual": 2 + (1 if a.kind == "nd3d" else 0), "jvp": 4}.get(a.op)
     line = {"kind": a.kind, "n": n, "levels": levels, "op": a.op, "dtype": a.dtype, "ms": ms}
+    if a.op == "solve":
+        line.update(newton_its=st["newton_its"], fgmres_its=st["linear_its"], converged=st["converged"])
     if stencils:
         line["ops_per_s"] = OPS_PER_ELEMENT[a.kind] * elems * stencils / (ms * 1e-3)
     if words:

@@ -1,0 +1,184 @@
+"""Pins of the oracle's version of the paper's own solver (CG outer method,
+coarse CG preconditioned by L-BFGS with the spectral shift of Alg. 1, Sec. 3
+settings) against facts fixed outside it: direct solves, finite termination,
+the hereditary property of BFGS updates with conjugate pairs, Rayleigh-quotient
+bounds from closed-form spectra, exact-Newton solutions and the counts the
+paper prints in Table 2."""
+import numpy as np
+import pytest
+
+from oracle import adjoint, jfnk
+
+
+def _spd(n, seed, lo=0.5, hi=20.0):
+    rng = np.random.default_rng(seed)
+    Q, _ = np.linalg.qr(rng.normal(size=(n, n)))
+    mu = np.linspace(lo, hi, n)
+    return Q @ np.diag(mu) @ Q.T, Q, mu
+
+
+def _ones_mask(n):
+    return np.ones(n, dtype=bool)
+
+
+def test_pcg_equals_direct_solve_and_terminates():
+    n = 30
+    A, _, _ = _spd(n, 1)
+    b = np.random.default_rng(2).normal(size=n)
+    x, its, res, neg = jfnk.pcg(lambda v: A @ v, b, _ones_mask(n), 1e-13, 5 * n)
+    assert not neg
+    assert np.linalg.norm(x - np.linalg.solve(A, b)) <= 1e-10 * np.linalg.norm(np.linalg.solve(A, b))
+    # n distinct eigenvalues: exact arithmetic terminates in n steps; rounding adds a few
+    assert its <= n + 5
+
+
+def test_pcg_exact_preconditioner_takes_one_step():
+    n = 25
+    A, _, _ = _spd(n, 3)
+    Ainv = np.linalg.inv(A)
+    b = np.random.default_rng(4).normal(size=n)
+    x, its, _, _ = jfnk.pcg(lambda v: A @ v, b, _ones_mask(n), 1e-10, 50, precond=lambda r: Ainv @ r)
+    assert its == 1
+    assert np.allclose(x, Ainv @ b, rtol=1e-10, atol=1e-12)
+
+
+def test_pcg_negative_curvature_exit():
+    # the first direction b has b.Ab < 0: return the first search direction
+    A = np.diag([-1.0, -2.0, 0.5])
+    b = np.ones(3)
+    x, its, _, neg = jfnk.pcg(lambda v: A @ v, b, _ones_mask(3), 1e-12, 10)
+    assert neg and its == 1 and np.array_equal(x, b)
+    # later negative curvature: the returned iterate is the last CG iterate,
+    # which reduces the quadratic model 1/2 x.Ax - b.x below 0
+    A = np.diag([4.0, 3.0, 2.0, -0.2])
+    b = np.array([1.0, 1.0, 1.0, 0.05])
+    x, its, _, neg = jfnk.pcg(lambda v: A @ v, b, _ones_mask(4), 1e-12, 10)
+    assert neg and its > 1
+    assert 0.5 * x @ A @ x - b @ x < 0.0
+
+
+def test_lbfgs_hereditary_property_and_full_inverse():
+    """BFGS updates with A-conjugate pairs y_i = A s_i satisfy H y_j = s_j for
+    every stored pair (hereditary property); with n such pairs H = A^-1."""
+    n = 12
+    A, Q, _ = _spd(n, 5)
+    rng = np.random.default_rng(6)
+    S = [Q[:, i] * rng.uniform(0.5, 2.0) for i in range(n)]  # eigenvectors: A-conjugate
+    mask = _ones_mask(n)
+    H = jfnk.LBFGS([(s, A @ s) for s in S[:7]], mask)
+    for s in S[:7]:
+        assert np.allclose(H.apply(A @ s), s, rtol=1e-11, atol=1e-12)
+    H = jfnk.LBFGS([(s, A @ s) for s in S], mask)
+    x = rng.normal(size=n)
+    assert np.allclose(H.apply(A @ x), x, rtol=1e-10, atol=1e-11)
+    # no pairs: the identity
+    assert np.array_equal(jfnk.LBFGS([], mask).apply(x), x)
+
+
+def test_uniform_sampling_indices():
+    pairs = list(range(50))
+    assert jfnk.uniform_sample(pairs, 20) == [(j * 50) // 20 for j in range(20)]
+    assert jfnk.uniform_sample(pairs, 20)[:4] == [0, 2, 5, 7]
+    assert jfnk.uniform_sample(pairs[:9], 20) == pairs[:9]
+
+
+class _Lv:
+    def __init__(self, n):
+        self.mask = np.ones(n, dtype=bool)
+        self.lbfgs = None
+
+
+def test_coarse_cgqn_spd_no_shift_and_lbfgs_speedup():
+    n = 40
+    A, _, _ = _spd(n, 7, lo=0.01, hi=10.0)
+    rng = np.random.default_rng(8)
+    lv = _Lv(n)
+    b = rng.normal(size=n)
+    s, shifts = jfnk.coarse_cgqn(lambda v: A @ v, b, lv, 1e-12, n * 3, 20, 5.0)
+    assert shifts == [0.0]
+    assert np.linalg.norm(A @ s - b) <= 1e-10 * np.linalg.norm(b)
+    assert lv.lbfgs is not None and len(lv.lbfgs.S) == 20
+    # the second call is preconditioned by the stored pairs: fewer CG steps
+    b2 = rng.normal(size=n)
+    _, _, its_plain = jfnk.coarse_cg(lambda v: A @ v, b2, lv.mask, np.zeros(n), 0.0, 1e-10, 3 * n)
+    _, _, its_qn = jfnk.coarse_cg(lambda v: A @ v, b2, lv.mask, np.zeros(n), 0.0, 1e-10, 3 * n, H=lv.lbfgs)
+    assert its_qn < its_plain
+
+
+def test_coarse_cgqn_spectral_shift_rule():
+    """Indefinite A: each shifted call starts from the returned s_0; the first
+    shift is gamma times a Rayleigh quotient, so it lies in
+    [gamma lambda_min(A), 0); every further shift is at least gamma times the
+    previous one; the final shifted operator is positive definite and s_0
+    solves it."""
+    rng = np.random.default_rng(9)
+    n = 20
+    Q, _ = np.linalg.qr(rng.normal(size=(n, n)))
+    mu = np.concatenate([[-0.3, -0.05], np.linspace(0.5, 4.0, n - 2)])
+    A = Q @ np.diag(mu) @ Q.T
+    b = rng.normal(size=n)
+    lv = _Lv(n)
+    gamma = 5.0
+    s, shifts = jfnk.coarse_cgqn(lambda v: A @ v, b, lv, 1e-12, 4 * n, 20, gamma)
+    assert len(shifts) >= 2 and shifts[0] == 0.0
+    assert gamma * mu.min() <= shifts[1] < 0.0
+    for a, c in zip(shifts[1:], shifts[2:]):
+        assert c <= gamma * a
+    As = A - shifts[-1] * np.eye(n)
+    assert np.linalg.eigvalsh(As).min() > 0.0
+    assert np.linalg.norm(As @ s - b) <= 1e-9 * np.linalg.norm(b)
+
+
+def _paper_bratu(n, levels, **kw):
+    lvs = jfnk.build_hierarchy("bratu2d", n, levels, lam=5.0)
+    o = jfnk.paper_options(**kw)
+    return jfnk.newton_solve(lvs, np.zeros((n + 1, n + 1)), o)
+
+
+def test_paper_variant_reaches_exact_newton_solution():
+    u, st = _paper_bratu(50, 2, atol_newton=1e-12)
+    assert st.converged
+    ud, _ = adjoint.newton_direct("bratu2d", np.zeros((51, 51)), lam=5.0)
+    assert np.linalg.norm(u - ud) <= 1e-8 * np.linalg.norm(ud)
+
+
+@pytest.mark.parametrize("n,levels", [(50, 2), (100, 3)])
+def test_paper_variant_newton_count_matches_table_2(n, levels):
+    """Table 2 prints 3 inexact-Newton iterations for Bratu at every refinement
+    level with ||F|| < 1e-6 (the discretisation here is Q1, not P1)."""
+    _, st = _paper_bratu(n, levels)
+    assert st.converged
+    assert st.newton_its == 3
+
+
+def test_paper_variant_ge_is_level_independent():
+    """Table 1: the GE count of CG-MG stays nearly constant under refinement."""
+    ges = [_paper_bratu(n, lv)[1].ge for n, lv in [(50, 2), (100, 3), (200, 4)]]
+    assert max(ges) <= 1.35 * min(ges)
+
+
+def test_lbfgs_initial_scaling():
+    """One pair: H r = (s.y / y.y) r for every r orthogonal to s and y."""
+    rng = np.random.default_rng(10)
+    s, y = rng.normal(size=6), rng.normal(size=6)
+    y = y + 2.0 * s  # s.y > 0
+    H = jfnk.LBFGS([(s, y)], _ones_mask(6))
+    r = rng.normal(size=6)
+    B = np.stack([s, y], axis=1)
+    r = r - B @ np.linalg.lstsq(B, r, rcond=None)[0]
+    assert np.allclose(H.apply(r), (s @ y) / (y @ y) * r, rtol=1e-12, atol=1e-14)
+
+
+def test_collected_pairs_are_secant_and_conjugate():
+    n = 30
+    A, _, _ = _spd(n, 11)
+    b = np.random.default_rng(12).normal(size=n)
+    pairs = []
+    jfnk.coarse_cg(lambda v: A @ v, b, _ones_mask(n), np.zeros(n), 0.0, 1e-12, 3 * n, collect=pairs)
+    assert len(pairs) >= 10
+    for s, y in pairs:
+        assert np.allclose(y, A @ s, rtol=1e-12, atol=1e-14)
+    S = np.stack([p[0] for p in pairs[:10]], axis=1)
+    G = S.T @ A @ S
+    off = G - np.diag(np.diag(G))
+    assert np.abs(off).max() <= 1e-8 * np.abs(np.diag(G)).max()
