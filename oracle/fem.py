@@ -21,6 +21,9 @@ Problems:
            (nonlinear diffusion -div((1+u^2) grad u) = f, manufactured from
            u* = sin(pi x) sin(pi y) sin(pi z))
   ndk3d    F_i = sum_e kappa_e int_e (1+u_h^2) grad u_h . grad phi_i - int 1 phi_i
+  minsurf2d F_i = int grad u_h . grad phi_i / sqrt(1 + |grad u_h|^2)   (Sec. 3, "Minimal
+           Surface": the gradient of Psi_M = int sqrt(1 + |grad u|^2)); Dirichlet data
+           u = 0 on x = 0 and x = 1, u = x(1-x) on y = 0 and y = 1 (minsurf_boundary)
 """
 import itertools
 
@@ -35,11 +38,11 @@ QW1 = np.array([0.5, 0.5])
 QP3 = np.array([0.5 - 0.5 * np.sqrt(0.6), 0.5, 0.5 + 0.5 * np.sqrt(0.6)])
 QW3 = np.array([5.0 / 18.0, 8.0 / 18.0, 5.0 / 18.0])
 
-KINDS = ("bratu2d", "nd3d", "ndk3d")
+KINDS = ("bratu2d", "nd3d", "ndk3d", "minsurf2d")
 
 
 def dim_of(kind):
-    return 2 if kind == "bratu2d" else 3
+    return 2 if kind in ("bratu2d", "minsurf2d") else 3
 
 
 def local_nodes(d):
@@ -153,6 +156,9 @@ def element_residual(kind, U, h, lam=0.0, kappa=None):
         if kind == "bratu2d":
             coef = 1.0
             src = -lam * np.exp(uq)
+        elif kind == "minsurf2d":
+            coef = 1.0 / np.sqrt(1.0 + sum(g * g for g in gq))
+            src = None
         else:
             coef = 1.0 + uq * uq
             if kind == "ndk3d":
@@ -221,6 +227,31 @@ def bratu_energy(u, lam):
         g = [sum(grad_phi(off, xi, h)[k] * U[off] for off in U) for k in range(2)]
         E += w * h * h * (0.5 * (g[0] ** 2 + g[1] ** 2) - lam * np.exp(uq))
     return float(E.sum())
+
+
+def minsurf_energy(u):
+    """Discrete area Psi_M(u_h) = int sqrt(1 + |grad u_h|^2) with the same Gauss
+    rule (Sec. 3, minimal surface); its gradient with respect to the interior
+    nodal values is F."""
+    n = u.shape[0] - 1
+    h = 1.0 / n
+    U = gather_element_values(u)
+    shape = next(iter(U.values())).shape
+    E = np.zeros(shape)
+    for xi, w in gauss_points(2):
+        g = [sum(grad_phi(off, xi, h)[k] * U[off] for off in U) for k in range(2)]
+        E += w * h * h * np.sqrt(1.0 + g[0] ** 2 + g[1] ** 2)
+    return float(E.sum())
+
+
+def minsurf_boundary(n):
+    """Node grid with the Dirichlet data of the minimal-surface example (Sec. 3):
+    u = x(1-x) on the edges y = 0 and y = 1, u = 0 on x = 0 and x = 1; interior 0."""
+    u = np.zeros((n + 1, n + 1))
+    x = np.linspace(0.0, 1.0, n + 1)
+    u[0, :] = x * (1.0 - x)
+    u[-1, :] = x * (1.0 - x)
+    return u
 
 
 # ---------------------------------------------------------------------------
@@ -340,6 +371,8 @@ def assemble_jacobian(kind, u, lam=0.0, kappa=None):
     replaced by zero (the unknowns are the interior nodes).  Written from the
     derivative of the element integrand:
       bratu2d  J_ab = int grad phi_b . grad phi_a - lam exp(u_h) phi_b phi_a
+      minsurf2d J_ab = int grad phi_b . grad phi_a / q - (grad u_h . grad phi_a)(grad u_h . grad phi_b) / q^3,
+               q = sqrt(1 + |grad u_h|^2)
       nd3d     J_ab = int (1+u_h^2) grad phi_b . grad phi_a + 2 u_h phi_b grad u_h . grad phi_a
       ndk3d    kappa_e times the nd3d integrand.
     """
@@ -362,6 +395,11 @@ def assemble_jacobian(kind, u, lam=0.0, kappa=None):
                 gab = sum(ga[k] * gb[k] for k in range(d))
                 if kind == "bratu2d":
                     val = gab - lam * np.exp(uq) * pb * pa
+                elif kind == "minsurf2d":
+                    q2 = 1.0 + sum(gq[k] * gq[k] for k in range(d))
+                    gua = sum(gq[k] * ga[k] for k in range(d))
+                    gub = sum(gq[k] * gb[k] for k in range(d))
+                    val = gab / np.sqrt(q2) - gua * gub / q2 ** 1.5
                 else:
                     val = (1.0 + uq * uq) * gab + 2.0 * uq * pb * sum(gq[k] * ga[k] for k in range(d))
                     if kind == "ndk3d":

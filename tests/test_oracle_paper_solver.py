@@ -7,7 +7,8 @@ paper prints in Table 2."""
 import numpy as np
 import pytest
 
-from oracle import adjoint, jfnk
+from golden import paper_tables
+from oracle import adjoint, fem, jfnk
 
 
 def _spd(n, seed, lo=0.5, hi=20.0):
@@ -142,13 +143,14 @@ def test_paper_variant_reaches_exact_newton_solution():
     assert np.linalg.norm(u - ud) <= 1e-8 * np.linalg.norm(ud)
 
 
-@pytest.mark.parametrize("n,levels", [(50, 2), (100, 3)])
-def test_paper_variant_newton_count_matches_table_2(n, levels):
-    """Table 2 prints 3 inexact-Newton iterations for Bratu at every refinement
-    level with ||F|| < 1e-6 (the discretisation here is Q1, not P1)."""
-    _, st = _paper_bratu(n, levels)
+@pytest.mark.parametrize("k", [1, 2])
+def test_paper_variant_newton_count_matches_table_2(k):
+    """Table 2 prints the inexact-Newton count for Bratu at every refinement
+    level L_k (25 * 2^k elements, k + 1 levels) with ||F|| < 1e-6; the Q1
+    discretisation here reproduces it."""
+    _, st = _paper_bratu(25 * 2 ** k, k + 1)
     assert st.converged
-    assert st.newton_its == 3
+    assert st.newton_its == paper_tables.load()[("table2", "bratu", "newton_its")][k - 1]
 
 
 def test_paper_variant_ge_is_level_independent():
@@ -182,3 +184,16 @@ def test_collected_pairs_are_secant_and_conjugate():
     G = S.T @ A @ S
     off = G - np.diag(np.diag(G))
     assert np.abs(off).max() <= 1e-8 * np.abs(np.diag(G)).max()
+
+
+@pytest.mark.parametrize("k", [1, 2, 3])
+def test_paper_variant_minimal_surface_ge_near_table_1(k):
+    """Minimal surface (Sec. 3) with the paper's solver: the GE count of CG-MG
+    is within 25 % of the one Table 1 prints for the same refinement level
+    (P1 there, Q1 here; the Newton counts differ more and are not pinned)."""
+    n = 25 * 2 ** k
+    lvs = jfnk.build_hierarchy("minsurf2d", n, k + 1)
+    _, st = jfnk.newton_solve(lvs, fem.minsurf_boundary(n), jfnk.paper_options())
+    assert st.converged
+    ge_paper = paper_tables.load()[("table1", "minsurf", "ge_cg_mg")][k - 1]
+    assert abs(st.ge - ge_paper) <= 0.25 * ge_paper, (st.ge, ge_paper)
