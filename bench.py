@@ -18,7 +18,9 @@ roofline: the dominant kernel (the FP64 element-residual kernel with the fused
          per-launch events, V-cycles replayed from their CUDA graph); FP64-ALU
          bound.
 extras:  also the 64-instance batched Bratu solve vs the same instances one by
-         one, and the forward + adjoint solve of the coefficient problem.
+         one, the forward + adjoint solve of the coefficient problem, and the
+         paper's own solver variant on Bratu and the minimal surface at its
+         refinement levels L1..L5.
 cpu_baseline / --impl reference: the CPU oracle timed on a bounded sample.
 
 Multi-GPU (torchrun, N > 1): replicas only -- every rank solves its own
@@ -53,10 +55,17 @@ def load_peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
-# FP64 pipe rate measured on this machine's GB300 with a register-resident FMA
-# chain (152 SMs x ~2 FP64 ops/clk): 0.60e12 operations/s.  The profile
-# summary under profiles/ gives the command.
-FP64_OPS_PEAK = 0.60e12
+# FP64 pipe peak derived from unit counts and clocks: 152 SMs x 2 FP64
+# instructions (add, mul or fma) per clock per SM (the per-SM peak ncu reports
+# for sm__sass_thread_inst_executed_op_dfma_pred_on) x the maximum SM clock;
+# 0.629e12 instructions/s at 2070 MHz (the nominal 1.25 TFLOP/s counts an FMA
+# as two flops).
+GB300_SMS = 152
+FP64_INST_PER_CLK_SM = 2
+
+
+def fp64_peak(peaks):
+    return GB300_SMS * FP64_INST_PER_CLK_SM * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
 
 
 class ClockSampler:
@@ -236,6 +245,41 @@ def adjoint_extra(jf, torch, n, shape, stream):
             "adjoint_fgmres_its": ast["linear_its"]}
 
 
+def paper_variant_extra(jf, torch, stream):
+    """The paper's own solver (outer CG, V(5,5), coarse CG with L-BFGS and the
+    spectral shift, ||F|| < 1e-6) on its two 2D examples, Bratu lambda = 5 and
+    the minimal surface, at the refinement levels L1..L5 of Sec. 3 (25 * 2^k
+    elements per direction, k + 1 levels): Newton and CG iterations, GE and
+    time to solution (CUDA events, one solve after one warm-up)."""
+    import numpy as np
+    rows = []
+    for kind in ("bratu2d", "minsurf2d"):
+        for k in range(1, 6):
+            n = 25 * 2 ** k
+            o = jf.paper_options()
+            p = jf.Problem(kind, n, k + 1, lam=5.0, options=o)
+            u0 = torch.zeros((n + 1, n + 1), dtype=torch.float64)
+            if kind == "minsurf2d":  # u = x(1-x) on y = 0, 1 and 0 on x = 0, 1 (Sec. 3)
+                x = torch.as_tensor(np.linspace(0.0, 1.0, n + 1))
+                u0[0, :] = x * (1.0 - x)
+                u0[-1, :] = x * (1.0 - x)
+            u0 = u0.cuda()
+            u = u0.clone()
+            p.solve(u)
+            torch.cuda.synchronize()
+            ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            u.copy_(u0)
+            ea.record(stream)
+            st = p.solve(u)
+            eb.record(stream)
+            torch.cuda.synchronize()
+            rows.append({"problem": kind, "level": f"L{k}", "n_elem": n, "mg_levels": k + 1,
+                         "newton_its": st["newton_its"], "cg_its": st["linear_its"], "ge": round(st["ge"], 1),
+                         "coarse_shifts": st["coarse_shifts"], "converged": st["converged"],
+                         "s": ea.elapsed_time(eb) * 1e-3})
+    return rows
+
+
 # ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
@@ -379,6 +423,7 @@ def main():
     # ---- batched workload and adjoint workload ---------------------------------
     batch = batched_extra(jf, torch)
     adj = adjoint_extra(jf, torch, n, shape, stream)
+    paper = paper_variant_extra(jf, torch, stream)
 
     # ---- roofline of the dominant kernel ---------------------------------------
     top = max(prof.items(), key=lambda kv: kv[1][1]) if prof else None
@@ -388,7 +433,7 @@ def main():
         avg_s = tot / cnt * 1e-3
         ops = ND_OPS_PER_ELEMENT * elems
         achieved = ops / avg_s / 1e12
-        peak = FP64_OPS_PEAK / 1e12
+        peak = fp64_peak(peaks) / 1e12
         total_ms_all = sum(v[1] for v in prof.values())
         roof = {"kernel": name, "bound": "alu", "achieved": achieved, "peak": peak,
                 "unit": "Top/s (fp64 pipe)", "frac": achieved / peak, "traffic": None,
@@ -396,7 +441,7 @@ def main():
                 "share_of_stencil_time": tot / total_ms_all if total_ms_all else None,
                 "timed_region": f"{args.steps} event-bracketed solves after the value's timed region "
                                 f"({ms_prof:.1f} ms per solve)",
-                "peak_source": "measured fp64 pipe rate of this pool's GB300 (bench docstring)"}
+                "peak_source": "derived: 152 SMs x 2 FP64 inst/clk x max SM clock (bench.py fp64_peak)"}
 
     cpu = None
     if rank == 0 and world == 1:
@@ -421,6 +466,7 @@ def main():
             "residual_eval": resid,
             "batched": batch,
             "adjoint": adj,
+            "paper_variant": paper,
             "e2e": {"value": e2e_ms * 1e-3, "unit": "s", "h2d_bytes_per_step": 8 * N, "d2h_bytes_per_step": 8 * N},
             "gpu_launches": int(launches),
             "roofline": roof,

@@ -55,8 +55,10 @@ typedef enum { JFNK_F32 = 0, JFNK_F64 = 1 } jfnk_dtype;
  *  JFNK_BRATU2D  F_i = int grad u.grad phi_i - lambda exp(u) phi_i   (Sec. 3, Bratu)
  *  JFNK_ND3D     F_i = int (1+u^2) grad u.grad phi_i - int f phi_i, f manufactured
  *                from u* = sin(pi x) sin(pi y) sin(pi z)
- *  JFNK_NDK3D    F_i = sum_e kappa_e int_e (1+u^2) grad u.grad phi_i - int phi_i   */
-typedef enum { JFNK_BRATU2D = 0, JFNK_ND3D = 1, JFNK_NDK3D = 2 } jfnk_kind;
+ *  JFNK_NDK3D    F_i = sum_e kappa_e int_e (1+u^2) grad u.grad phi_i - int phi_i
+ *  JFNK_MINSURF2D F_i = int grad u.grad phi_i / sqrt(1 + |grad u|^2)  (Sec. 3, minimal
+ *                surface; its Dirichlet data x(1-x) / 0 are the boundary entries of u) */
+typedef enum { JFNK_BRATU2D = 0, JFNK_ND3D = 1, JFNK_NDK3D = 2, JFNK_MINSURF2D = 3 } jfnk_kind;
 
 /* Finite-difference step (Sec. 1):
  *  JFNK_EPS_PAPER  eps = (1/(n ||v||_2)) sum_i sqrt(eps_p)(1+|x_i|), eps_p = 2^-52,
@@ -99,7 +101,16 @@ typedef struct {
     int ls_max;              /* backtracking steps */
     uint64_t seed;           /* power-method start vector (SplitMix64 stream) */
     int use_graph;           /* 1: capture the V-cycle once in a CUDA graph and replay it */
+    /* The paper's own solver variant (Sec. 2 "The coarse level solver", Alg. 1, Sec. 3) */
+    int outer;               /* JFNK_OUTER_FGMRES (configured workloads) or JFNK_OUTER_CG (Sec. 3) */
+    int coarse_method;       /* JFNK_COARSE_GMRES or JFNK_COARSE_CGQN: CG preconditioned by L-BFGS,
+                                stopped on negative curvature, re-run with the spectral shift (Alg. 1) */
+    int lbfgs_pairs;         /* secant pairs kept for the L-BFGS preconditioner (Sec. 3: 20; <= 32) */
+    double shift_gamma;      /* gamma of the shift update lambda_c+ = gamma min(lambda_c, lambda_c+) (Sec. 3: 5) */
 } jfnk_options;
+
+typedef enum { JFNK_OUTER_FGMRES = 0, JFNK_OUTER_CG = 1 } jfnk_outer;
+typedef enum { JFNK_COARSE_GMRES = 0, JFNK_COARSE_CGQN = 1 } jfnk_coarse_method;
 
 #define JFNK_MAX_LEVELS 16
 #define JFNK_MAX_HIST 64
@@ -116,11 +127,22 @@ typedef struct {
     long long nF[JFNK_MAX_LEVELS];       /* residual evaluations per level (incl. FD actions) */
     double lambda_max[JFNK_MAX_LEVELS];  /* last power-method estimates */
     double setup_ms, solve_ms;
+    int coarse_shifts;                   /* shifted coarse CG calls (Alg. 1 while-loop) */
+    int coarse_negcurv;                  /* coarse CG calls ended by negative curvature */
+    int outer_negcurv;                   /* outer CG solves ended by negative curvature */
 } jfnk_stats;
 
 /* Defaults of the 2D Bratu workload: V(3,3), degree 3, [0.1, 1.1] lambda_max,
  * 10 power iterations, FGMRES(30), rtol 1e-10, FP64 preconditioner. */
 void jfnk_default_options(jfnk_options* opts);
+
+/* The paper's own settings (Sec. 2, Sec. 3 "Setup"): outer CG preconditioned by
+ * one V(5,5) cycle (read as one degree-5 Chebyshev application per side),
+ * interval [0.06, 1.2] lambda_l, power method to 30 iterations or a relative
+ * change below 1e-2, coarse CG with 20 L-BFGS secant pairs and the spectral
+ * shift gamma = 5, eta = min(0.5, ||F||), stop at ||F|| < 1e-6, FP64.
+ * The paper has no counterpart of use_graph (left at 1). */
+void jfnk_paper_options(jfnk_options* opts);
 
 /* Create / destroy a problem description on the current CUDA device.
  * Allocates only host memory.  INVALID_ARG on bad kind/sizes/levels. */
@@ -162,11 +184,15 @@ jfnk_status jfnk_mg_setup(jfnk_problem* p, const jfnk_options* opts, const doubl
 jfnk_status jfnk_mg_vcycle(jfnk_problem* p, const jfnk_options* opts, const double* b, double* s, void* stream);
 
 /* Inexact JFNK solve (Sec. 1, Sec. 3): Newton with MG-preconditioned FGMRES(m)
- * and backtracking; u_inout (FP64) is the initial guess with its Dirichlet data
- * on the boundary and receives the solution.  stats may be NULL. */
+ * (opts->outer = JFNK_OUTER_FGMRES) or CG (JFNK_OUTER_CG, the paper's choice;
+ * negative curvature p.Jp <= 0 ends it with the current iterate, or the first
+ * search direction at the first iteration) and backtracking; u_inout (FP64) is
+ * the initial guess with its Dirichlet data on the boundary and receives the
+ * solution.  stats may be NULL. */
 jfnk_status jfnk_solve(jfnk_problem* p, const jfnk_options* opts, double* u_inout, jfnk_stats* stats, void* stream);
 
-/* Batched solve of `count` independent 2D Bratu problems of uneven sizes and
+/* Batched solve (FGMRES outer and GMRES coarse solves only; NOT_IMPLEMENTED
+ * otherwise) of `count` independent 2D Bratu problems of uneven sizes and
  * parameters (e.g. 129^2 / 257^2 / 513^2 nodes, different lambda) whose
  * hierarchies end at the same coarse grid.  Each problem keeps its own
  * workspace (laid out for opts); u_inout[i] is instance i's iterate.  The
@@ -199,8 +225,15 @@ jfnk_status jfnk_transfer(jfnk_problem* p, int op, int level, int dtype, const v
 jfnk_status jfnk_smooth(jfnk_problem* p, const jfnk_options* opts, int level, const void* b, void* s, int nu,
                         int s_is_zero, void* stream);
 
-/* Coarse solve of Algorithm 1 on level 0 (Sec. 2, "The coarse level solver";
- * GMRES in one CTA).  Vectors in opts->pc_dtype.  Requires jfnk_mg_setup. */
+/* Coarse solve of Algorithm 1 on level 0 (Sec. 2, "The coarse level solver"),
+ * in one CTA: GMRES (opts->coarse_method = JFNK_COARSE_GMRES) or the paper's
+ * CG preconditioned by L-BFGS with the spectral shift (JFNK_COARSE_CGQN): the
+ * first call after jfnk_mg_setup(newton_step = 0) collects the secant pairs and
+ * keeps opts->lbfgs_pairs of them (uniform sampling) for every later call; a
+ * CG run that meets negative curvature is repeated on A - lambda_c+ I with
+ * lambda_c+ = shift_gamma min(lambda_c, lambda_c+) (at most 30 times).  The
+ * adjoint solve always uses GMRES.  Vectors in opts->pc_dtype.  Requires
+ * jfnk_mg_setup. */
 jfnk_status jfnk_coarse_solve(jfnk_problem* p, const jfnk_options* opts, const void* b, void* s, void* stream);
 
 /* Host copies of the level scalars set by jfnk_mg_setup: lambda_l (power
@@ -268,7 +301,7 @@ jfnk_status jfnk_jvp_noalloc(int kind, int n_elem, double lambda, const void* ka
 
 /* Limits of the single-CTA coarse solver and of FGMRES. */
 #define JFNK_COARSE_MAX_NODES 1024
-#define JFNK_COARSE_MAX_IT 512
+#define JFNK_COARSE_MAX_IT 1024
 #define JFNK_MAX_RESTART 64
 
 /* Message for the last error on the calling thread. */

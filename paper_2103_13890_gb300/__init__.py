@@ -17,7 +17,8 @@ import ctypes
 import torch
 
 from . import _abi
-from ._abi import BRATU2D, EPS_FP32, EPS_PAPER, F32, F64, KINDS, ND3D, NDK3D  # noqa: F401
+from ._abi import (BRATU2D, COARSE_CGQN, COARSE_GMRES, EPS_FP32, EPS_PAPER, F32, F64, KINDS,  # noqa: F401
+                   MINSURF2D, ND3D, NDK3D, OUTER_CG, OUTER_FGMRES)
 
 _LIB = None
 
@@ -52,6 +53,19 @@ def default_options(**kw):
     """jfnk_options with the library defaults, overridden by keyword."""
     o = _abi.Options()
     lib().jfnk_default_options(ctypes.byref(o))
+    return _override(o, kw)
+
+
+def paper_options(**kw):
+    """jfnk_options with the paper's own settings (jfnk_paper_options: CG outer,
+    V(5,5), [0.06, 1.2] lambda, coarse CG with L-BFGS and spectral shift,
+    ||F|| < 1e-6), overridden by keyword."""
+    o = _abi.Options()
+    lib().jfnk_paper_options(ctypes.byref(o))
+    return _override(o, kw)
+
+
+def _override(o, kw):
     for k, v in kw.items():
         if k == "pc_dtype" and isinstance(v, torch.dtype):
             v = F32 if v == torch.float32 else F64
@@ -76,13 +90,14 @@ def stats_dict(s):
         "converged": bool(s.converged), "res_hist": list(s.res_hist[:L + 1]),
         "alpha_hist": list(s.alpha_hist[:L]), "lin_hist": list(s.lin_hist[:L]), "ge": s.ge,
         "nF": list(s.nF), "lambda_max": list(s.lambda_max), "solve_ms": s.solve_ms,
+        "coarse_shifts": s.coarse_shifts, "coarse_negcurv": s.coarse_negcurv, "outer_negcurv": s.outer_negcurv,
     }
 
 
 class Problem:
     """One discretised problem on the current CUDA device with its workspace.
 
-    kind: "bratu2d" | "nd3d" | "ndk3d"; n_elem: finest elements per direction;
+    kind: "bratu2d" | "nd3d" | "ndk3d" | "minsurf2d"; n_elem: finest elements per direction;
     levels: multigrid levels; lam: Bratu lambda; load: optional FP64 finest
     load vector (nd3d); kappa: FP64 per-element coefficient (ndk3d, n_elem^3).
     options: the jfnk_options the workspace is laid out for (None: residual and
@@ -90,7 +105,7 @@ class Problem:
 
     def __init__(self, kind, n_elem, levels, lam=0.0, load=None, kappa=None, options=None, device="cuda"):
         self.kind = kind
-        self.d = 2 if kind == "bratu2d" else 3
+        self.d = 2 if kind in ("bratu2d", "minsurf2d") else 3
         self.n = n_elem
         self.levels = levels
         self.device = torch.device(device)

@@ -12,10 +12,12 @@ OK = 0
 STATUS = {0: "OK", 1: "INVALID_ARG", 2: "CUDA", 3: "NONFINITE", 4: "NOT_CONVERGED", 5: "BREAKDOWN",
           6: "LINESEARCH", 7: "TIMEOUT", 8: "NOT_IMPLEMENTED", 9: "WORKSPACE"}
 F32, F64 = 0, 1
-BRATU2D, ND3D, NDK3D = 0, 1, 2
-KINDS = {"bratu2d": BRATU2D, "nd3d": ND3D, "ndk3d": NDK3D}
+BRATU2D, ND3D, NDK3D, MINSURF2D = 0, 1, 2, 3
+KINDS = {"bratu2d": BRATU2D, "nd3d": ND3D, "ndk3d": NDK3D, "minsurf2d": MINSURF2D}
 EPS_PAPER, EPS_FP32 = 0, 1
 RESTRICT, PROLONG_ADD, PROJECT = 0, 1, 2
+OUTER_FGMRES, OUTER_CG = 0, 1
+COARSE_GMRES, COARSE_CGQN = 0, 1
 
 
 class ProblemDesc(ctypes.Structure):
@@ -31,7 +33,9 @@ class Options(ctypes.Structure):
                 ("eta_max", ctypes.c_double), ("coarse_tol", ctypes.c_double), ("coarse_tol_mode", ctypes.c_int),
                 ("coarse_maxit", ctypes.c_int), ("pc_dtype", ctypes.c_int), ("eps_mode_pc", ctypes.c_int),
                 ("max_newton", ctypes.c_int), ("line_search", ctypes.c_int), ("ls_max", ctypes.c_int),
-                ("seed", ctypes.c_uint64), ("use_graph", ctypes.c_int)]
+                ("seed", ctypes.c_uint64), ("use_graph", ctypes.c_int),
+                ("outer", ctypes.c_int), ("coarse_method", ctypes.c_int), ("lbfgs_pairs", ctypes.c_int),
+                ("shift_gamma", ctypes.c_double)]
 
 
 class Stats(ctypes.Structure):
@@ -40,13 +44,15 @@ class Stats(ctypes.Structure):
                 ("alpha_hist", ctypes.c_double * MAX_HIST), ("lin_hist", ctypes.c_int * MAX_HIST),
                 ("ge", ctypes.c_double), ("nF", ctypes.c_longlong * MAX_LEVELS),
                 ("lambda_max", ctypes.c_double * MAX_LEVELS), ("setup_ms", ctypes.c_double),
-                ("solve_ms", ctypes.c_double)]
+                ("solve_ms", ctypes.c_double), ("coarse_shifts", ctypes.c_int),
+                ("coarse_negcurv", ctypes.c_int), ("outer_negcurv", ctypes.c_int)]
 
 
 # (name, restype, argtypes) of every exported symbol declared in include/jfnk.h
 _vp, _i, _d = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
 SIGNATURES = [
     ("jfnk_default_options", None, [ctypes.POINTER(Options)]),
+    ("jfnk_paper_options", None, [ctypes.POINTER(Options)]),
     ("jfnk_problem_create", _i, [ctypes.POINTER(ProblemDesc), ctypes.POINTER(_vp)]),
     ("jfnk_problem_destroy", _i, [_vp]),
     ("jfnk_workspace_size", _i, [_vp, ctypes.POINTER(Options), ctypes.POINTER(ctypes.c_size_t)]),

@@ -13,72 +13,13 @@
 #include "element.cuh"
 #include "reduce.cuh"
 #include "stencil.cuh"
+#include "stencil_body.cuh"
+#include "stencil_ep.cuh"
 
 namespace jfnk {
 
 constexpr int KA_BX = 32, KA_BY = 8, KA_TX = KA_BX - 1, KA_TY = KA_BY - 1;
 constexpr int KA_WX = KA_BX + 1, KA_WY = KA_BY + 1;
-
-template <typename T>
-struct ChebKA {
-    T theta_inv, c1, c2;
-};
-template <typename T>
-__device__ __forceinline__ ChebKA<T> cheb_ofa(const ChebTable* t, int i);
-template <>
-__device__ __forceinline__ ChebKA<double> cheb_ofa<double>(const ChebTable* t, int i) {
-    return {t->theta_inv, t->c1[i], t->c2[i]};
-}
-template <>
-__device__ __forceinline__ ChebKA<float> cheb_ofa<float>(const ChebTable* t, int i) {
-    return {t->theta_invf, t->c1f[i], t->c2f[i]};
-}
-
-// jd = (J^T v)_i at an interior node (0 on the boundary)
-template <typename T, Mode M>
-__device__ __forceinline__ void epilogue_adj(const StencilArgs<T>& a, long long idx, bool inner, T jd,
-                                             const ChebKA<T>& ck, float& red) {
-    if (M == Mode::JV) {
-        const T o = inner ? jd : T(0);
-        a.out[idx] = o;
-        red += (float)o * (float)o;
-    } else if (M == Mode::BMJ) {
-        const T o = inner ? a.rhs[idx] - jd : T(0);
-        a.out[idx] = o;
-        red += (float)o * (float)o;
-    } else if (M == Mode::CHEB0) {
-        T rr = T(0), dd = T(0);
-        if (inner) {
-            rr = a.rhs[idx] - jd;
-            dd = rr * ck.theta_inv;
-        }
-        a.out[idx] = rr;
-        a.out2[idx] = dd;
-        red += (float)dd * (float)dd;
-    } else if (M == Mode::CHEB) {
-        T rr = T(0), ss = T(0), dn = T(0);
-        if (inner) {
-            const T dc = a.v[idx];
-            rr = a.r[idx] - jd;
-            ss = a.s[idx] + dc;
-            dn = ck.c1 * dc + ck.c2 * rr;
-        }
-        a.r[idx] = rr;
-        a.s[idx] = ss;
-        a.dnew[idx] = dn;
-        red += (float)dn * (float)dn;
-    } else if (M == Mode::CHEBLAST) {
-        T ss = T(0);
-        if (inner) {
-            const T dc = a.v[idx];
-            const T rr = a.r[idx] - jd;
-            const T dn = ck.c1 * dc + ck.c2 * rr;
-            ss = a.s[idx] + dc + dn;
-        }
-        a.s[idx] = ss;
-        red += (float)ss * (float)ss;
-    }
-}
 
 template <typename T, bool KAPPA, Mode M>
 __global__ void __launch_bounds__(KA_BX* KA_BY) vjp3d_kernel(const StencilArgs<T> a, int zchunk) {
@@ -92,8 +33,8 @@ __global__ void __launch_bounds__(KA_BX* KA_BY) vjp3d_kernel(const StencilArgs<T
     const int x0 = blockIdx.x * KA_TX, y0 = blockIdx.y * KA_TY;
     const int z0 = blockIdx.z * zchunk;
     const int z1 = min(z0 + zchunk, g.nz);
-    ChebKA<T> ck = {T(0), T(0), T(0)};
-    if (M == Mode::CHEB0 || M == Mode::CHEB || M == Mode::CHEBLAST) ck = cheb_ofa<T>(a.cheb, a.cheb_step);
+    ChebK<T> ck = {T(0), T(0), T(0)};
+    if (M == Mode::CHEB0 || M == Mode::CHEB || M == Mode::CHEBLAST) ck = cheb_of<T>(a.cheb, a.cheb_step);
     const int ex = x0 - 1 + tx, ey = y0 - 1 + ty;
     const bool elem_xy = ex >= 0 && ex < n && ey >= 0 && ey < n;
     const int nx_o = x0 + tx, ny_o = y0 + ty;
@@ -208,6 +149,7 @@ static jfnk_status launch_vjp_k(Mode mode, const StencilArgs<T>& a, cudaStream_t
 
 template <typename T>
 jfnk_status launch_vjp(Prob prob, Mode mode, const StencilArgs<T>& a, cudaStream_t st) {
+    if ((prob == Prob::NDK3 || prob == Prob::ND3) && ep3d_use(a)) return launch_ep3d<T>(prob, mode, true, a, st);
     if (prob == Prob::NDK3) return launch_vjp_k<T, true>(mode, a, st);
     if (prob == Prob::ND3) return launch_vjp_k<T, false>(mode, a, st);
     set_error("the adjoint operator is implemented for the 3D diffusion problems");

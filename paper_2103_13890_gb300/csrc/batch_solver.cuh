@@ -1289,6 +1289,10 @@ jfnk_status jfnk_solve_batched(jfnk_problem* const* problems, int count, const j
         set_error("jfnk_solve_batched: empty batch");
         return JFNK_ERR_INVALID_ARG;
     }
+    if (opts && (opts->outer != JFNK_OUTER_FGMRES || opts->coarse_method != JFNK_COARSE_GMRES)) {
+        set_error("jfnk_solve_batched: FGMRES outer and GMRES coarse solves only");
+        return JFNK_ERR_NOT_IMPLEMENTED;
+    }
     for (int i = 0; i < count; ++i) {
         JFNK_TRY(need_solver(problems[i], opts));
         const P& p = *problems[i];

@@ -22,14 +22,17 @@ __device__ void coarse_apply_A(const Grid& g, const T* w, T* elemC, T* out, cons
     // elemC: [nelem][2^d];  out: A(w) scaled, full grid (boundary entries untouched)
     const int n = g.n;
     const int tid = threadIdx.x;
-    if (P == Prob::BRATU2) {
+    if (is_2d(P)) {
         const int ne = n * n;
         for (int e = tid; e < ne; e += blockDim.x) {
             const int ex = e % n, ey = e / n;
             const long long b = (long long)ey * g.sy + ex;
             T ue[4] = {w[b], w[b + 1], w[b + g.sy], w[b + g.sy + 1]};
             T r[4];
-            elem_bratu2<T>(ue, lh, r);
+            if (P == Prob::MINSURF2)
+                elem_minsurf2<T>(ue, lh, r);
+            else
+                elem_bratu2<T>(ue, lh, r);
 #pragma unroll
             for (int c = 0; c < 4; ++c) elemC[e * 4 + c] = r[c];
         }
@@ -288,6 +291,288 @@ __device__ void coarse_gmres_body(const CoarseArgs<T>& a, unsigned char* smem_ra
     }
 }
 
+// ---------------------------------------------------------------------------
+// The paper's coarse solver (Sec. 2 "The coarse level solver", Alg. 1, l = 0):
+// CG preconditioned by L-BFGS, stopped on negative curvature, and re-run on the
+// shifted operator A_s = A - lambda_c+ I (lambda_c+ <= 0) with
+// lambda_c+ <- gamma min(lambda_c, lambda_c+) while the Rayleigh quotient
+// lambda_c = p.A_s p / p.p of the direction of negative curvature is < 0.
+// The secant pairs (s_i, y_i) = (alpha_i p_i, alpha_i A p_i) of the very first
+// call are collected; m of the k steps, those of iterations floor(j k / m),
+// are kept (uniform sampling) and define the preconditioner for the rest of
+// the solve.  Each shifted call restarts CG from the returned s_0.  At most
+// 30 shifted calls.  All of it runs in one CTA.
+// ---------------------------------------------------------------------------
+constexpr int kMaxShiftCalls = 30;
+
+// block-wide interior dot product, result in every thread
+template <typename T>
+__device__ double cg_dot(const Grid& g, const T* a, const T* b, int N, double* red, double* bc) {
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < N; i += blockDim.x)
+        if (coarse_inner(g, i)) acc += (double)a[i] * (double)b[i];
+    const double t = block_sum(acc, red);
+    if (threadIdx.x == 0) *bc = t;
+    __syncthreads();
+    const double r = *bc;
+    __syncthreads();
+    return r;
+}
+
+// q = A_s p = (A(x_0 + eps p) - A(x_0)) / eps - shift p on interior nodes, 0 on the boundary
+template <typename T, Prob P>
+__device__ void cg_apply(const CoarseArgs<T>& a, const T* p, T* q, T* xw, T* Aw, T* elemC, double shift,
+                         double xstat, double* red, double* bc) {
+    const Grid g = a.g;
+    const int N = (int)g.size;
+    const double pn = sqrt(cg_dot(g, p, p, N, red, bc));
+    const double e = eps_formula(a.eps_mode, a.n_unknowns, xstat, pn);
+    if (!(e > 0.0) || !isfinite(e)) {
+        for (int i = threadIdx.x; i < N; i += blockDim.x) q[i] = T(0);
+        __syncthreads();
+        return;
+    }
+    const T eps = (T)e, inv = (T)(1.0 / e), sh = (T)shift;
+    for (int i = threadIdx.x; i < N; i += blockDim.x) xw[i] = a.x[i] + (coarse_inner(g, i) ? eps * p[i] : T(0));
+    __syncthreads();
+    coarse_apply_A<T, P>(g, xw, elemC, Aw, a.kappa, a.lh, a.node_scale);
+    for (int i = threadIdx.x; i < N; i += blockDim.x)
+        q[i] = coarse_inner(g, i) ? (Aw[i] - a.Ax[i]) * inv - sh * p[i] : T(0);
+    __syncthreads();
+}
+
+// z = H r with the compact L-BFGS form (k kept pairs; k = 0: z = r)
+template <typename T>
+__device__ void cg_precond(const CoarseArgs<T>& a, const T* r, T* z, int k, double* dots, double* coef) {
+    const Grid g = a.g;
+    const int N = (int)g.size;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nwarps = blockDim.x >> 5;
+    if (k <= 0) {
+        for (int i = tid; i < N; i += blockDim.x) z[i] = r[i];
+        __syncthreads();
+        return;
+    }
+    const LbfgsState* lb = a.lb;
+    for (int q = wid; q < 2 * k; q += nwarps) {
+        const T* v = (q < k) ? a.S + (long long)q * N : a.Y + (long long)(q - k) * N;
+        double d = 0.0;
+        for (int i = lane; i < N; i += 32) d += (double)v[i] * (double)r[i];
+        d = warp_sum(d);
+        if (lane == 0) dots[q] = d;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        const double gam = lb->gamma;
+        double t[kMaxLbfgsPairs], v[kMaxLbfgsPairs];
+        // t = R^-1 (S^T r)
+        for (int i = k - 1; i >= 0; --i) {
+            double acc = dots[i];
+            for (int j = i + 1; j < k; ++j) acc -= lb->R[i * kMaxLbfgsPairs + j] * t[j];
+            t[i] = acc / lb->R[i * kMaxLbfgsPairs + i];
+        }
+        // v = (D + gamma Y^T Y) t - gamma Y^T r
+        for (int i = 0; i < k; ++i) {
+            double acc = lb->R[i * kMaxLbfgsPairs + i] * t[i];
+            for (int j = 0; j < k; ++j) acc += gam * lb->YtY[i * kMaxLbfgsPairs + j] * t[j];
+            v[i] = acc - gam * dots[k + i];
+        }
+        // top = R^-T v ; coefficients of S (top) and of Y (-gamma t)
+        for (int i = 0; i < k; ++i) {
+            double acc = v[i];
+            for (int j = 0; j < i; ++j) acc -= lb->R[j * kMaxLbfgsPairs + i] * coef[j];
+            coef[i] = acc / lb->R[i * kMaxLbfgsPairs + i];
+        }
+        for (int i = 0; i < k; ++i) coef[k + i] = -gam * t[i];
+        coef[2 * k] = gam;
+    }
+    __syncthreads();
+    const double gam = coef[2 * k];
+    for (int i = tid; i < N; i += blockDim.x) {
+        double acc = gam * (double)r[i];
+        for (int j = 0; j < k; ++j)
+            acc += coef[j] * (double)a.S[(long long)j * N + i] + coef[k + j] * (double)a.Y[(long long)j * N + i];
+        z[i] = coarse_inner(g, i) ? (T)acc : T(0);
+    }
+    __syncthreads();
+}
+
+struct CgOut {
+    double lam_c;  // Rayleigh quotient at negative curvature, else 0
+    int its;
+    int fd;        // FD actions (level-0 gradient evaluations)
+    int negcurv;
+};
+
+// CG(s_0, x_0, F(x_0), r_0, lambda_c+) of Alg. 1 on the vectors in shared memory
+template <typename T, Prob P>
+__device__ CgOut coarse_cg_run(const CoarseArgs<T>& a, T* x, T* r, T* z, T* pv, T* q, T* xw, T* Aw, T* elemC,
+                               double shift, bool warm, int kpre, bool collect, double xstat, double target,
+                               double* red, double* bc, double* dots, double* coef) {
+    const Grid g = a.g;
+    const int N = (int)g.size;
+    const int tid = threadIdx.x;
+    CgOut o = {0.0, 0, 0, 0};
+    if (warm) {
+        cg_apply<T, P>(a, x, q, xw, Aw, elemC, shift, xstat, red, bc);
+        o.fd++;
+        for (int i = tid; i < N; i += blockDim.x) r[i] = coarse_inner(g, i) ? a.b[i] - q[i] : T(0);
+    } else {
+        for (int i = tid; i < N; i += blockDim.x) r[i] = coarse_inner(g, i) ? a.b[i] : T(0);
+    }
+    __syncthreads();
+    double res = sqrt(cg_dot(g, r, r, N, red, bc));
+    if (!(res > 0.0) || res <= target || !isfinite(res)) return o;
+    cg_precond<T>(a, r, z, kpre, dots, coef);
+    double rz = cg_dot(g, r, z, N, red, bc);
+    for (int i = tid; i < N; i += blockDim.x) pv[i] = z[i];
+    __syncthreads();
+    for (int it = 1; it <= a.maxit; ++it) {
+        cg_apply<T, P>(a, pv, q, xw, Aw, elemC, shift, xstat, red, bc);
+        o.fd++;
+        o.its = it;
+        const double pq = cg_dot(g, pv, q, N, red, bc);
+        if (!isfinite(pq)) return o;
+        if (pq <= 0.0) {
+            const double pp = cg_dot(g, pv, pv, N, red, bc);
+            o.lam_c = pp > 0.0 ? pq / pp : 0.0;
+            o.negcurv = 1;
+            return o;
+        }
+        const double alpha = rz / pq;
+        const T al = (T)alpha;
+        for (int i = tid; i < N; i += blockDim.x) {
+            if (collect) {
+                a.S_all[(long long)(it - 1) * N + i] = al * pv[i];
+                a.Y_all[(long long)(it - 1) * N + i] = al * q[i];
+            }
+            x[i] += al * pv[i];
+            r[i] -= al * q[i];
+        }
+        if (collect && tid == 0) a.lb->collected = it;
+        __syncthreads();
+        res = sqrt(cg_dot(g, r, r, N, red, bc));
+        if (res <= target || !isfinite(res)) return o;
+        cg_precond<T>(a, r, z, kpre, dots, coef);
+        const double rz_new = cg_dot(g, r, z, N, red, bc);
+        const T beta = (T)(rz_new / rz);
+        rz = rz_new;
+        for (int i = tid; i < N; i += blockDim.x) pv[i] = z[i] + beta * pv[i];
+        __syncthreads();
+    }
+    return o;
+}
+
+// keep m of the collected pairs (uniform sampling) and set up the compact form
+template <typename T>
+__device__ void lbfgs_build(const CoarseArgs<T>& a, double* red, double* bc) {
+    const Grid g = a.g;
+    const int N = (int)g.size;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nwarps = blockDim.x >> 5;
+    LbfgsState* lb = a.lb;
+    const int kall = lb->collected;
+    const int m = min(a.m_pairs, kMaxLbfgsPairs);
+    const int k = min(kall, m);
+    for (int j = 0; j < k; ++j) {
+        const long long src = (kall > m) ? ((long long)j * kall) / m : j;
+        for (int i = tid; i < N; i += blockDim.x) {
+            a.S[(long long)j * N + i] = a.S_all[src * N + i];
+            a.Y[(long long)j * N + i] = a.Y_all[src * N + i];
+        }
+    }
+    __syncthreads();
+    // R_ij = s_i.y_j (i <= j), YtY_ij = y_i.y_j
+    for (int q = wid; q < 2 * k * k; q += nwarps) {
+        const int which = q / (k * k), ij = q % (k * k), i = ij / k, j = ij % k;
+        const T* u = (which == 0) ? a.S + (long long)i * N : a.Y + (long long)i * N;
+        const T* v = a.Y + (long long)j * N;
+        double d = 0.0;
+        for (int t = lane; t < N; t += 32) d += (double)u[t] * (double)v[t];
+        d = warp_sum(d);
+        if (lane == 0) {
+            if (which == 0)
+                lb->R[i * kMaxLbfgsPairs + j] = (i <= j) ? d : 0.0;
+            else
+                lb->YtY[i * kMaxLbfgsPairs + j] = d;
+        }
+    }
+    __syncthreads();
+    if (tid == 0) {
+        bool ok = k > 0;
+        for (int i = 0; i < k; ++i) ok = ok && lb->R[i * kMaxLbfgsPairs + i] > 0.0;
+        const double yy = k > 0 ? lb->YtY[(k - 1) * kMaxLbfgsPairs + (k - 1)] : 0.0;
+        lb->gamma = (ok && yy > 0.0) ? lb->R[(k - 1) * kMaxLbfgsPairs + (k - 1)] / yy : 1.0;
+        lb->count = (ok && yy > 0.0) ? k : 0;
+    }
+    __syncthreads();
+}
+
+template <typename T, Prob P>
+__global__ void __launch_bounds__(kCoarseThreads) coarse_cgqn_kernel(CoarseArgs<T> a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const Grid g = a.g;
+    const int N = (int)g.size;
+    const int ne = (g.d == 3) ? g.n * g.n * g.n : g.n * g.n;
+    const int npe = (g.d == 3) ? 8 : 4;
+    T* x = reinterpret_cast<T*>(smem_raw);
+    T* r = x + N;
+    T* z = r + N;
+    T* pv = z + N;
+    T* q = pv + N;
+    T* xw = q + N;
+    T* Aw = xw + N;
+    T* elemC = Aw + N;
+    double* dd = reinterpret_cast<double*>((reinterpret_cast<uintptr_t>(elemC + ne * npe) + 15) & ~uintptr_t(15));
+    double* dots = dd;                        // [2 kMax]
+    double* coef = dots + 2 * kMaxLbfgsPairs;  // [2 kMax + 1]
+    double* red = coef + 2 * kMaxLbfgsPairs + 2;  // [32]
+    __shared__ double bc;
+    __shared__ int s_count;
+    const int tid = threadIdx.x;
+    const double xstat = *a.xstat;
+    const double bn = sqrt(cg_dot(g, a.b, a.b, N, red, &bc));
+    const double target = a.tol_abs ? a.tol : a.tol * bn;
+    for (int i = tid; i < N; i += blockDim.x) x[i] = T(0);
+    if (tid == 0) s_count = a.lb->count;
+    __syncthreads();
+    const bool collect = s_count < 0;
+    long long fd = 0;
+    int negc = 0;
+    double shift = 0.0;
+    CgOut o = coarse_cg_run<T, P>(a, x, r, z, pv, q, xw, Aw, elemC, shift, false, collect ? 0 : s_count, collect,
+                                  xstat, target, red, &bc, dots, coef);
+    fd += o.fd;
+    negc += o.negcurv;
+    if (collect) {
+        lbfgs_build<T>(a, red, &bc);
+        if (tid == 0) s_count = a.lb->count;
+        __syncthreads();
+    }
+    int nshift = 0;
+    while (o.lam_c < 0.0 && nshift < kMaxShiftCalls) {
+        shift = a.shift_gamma * fmin(o.lam_c, shift);
+        ++nshift;
+        o = coarse_cg_run<T, P>(a, x, r, z, pv, q, xw, Aw, elemC, shift, true, s_count, false, xstat, target, red,
+                                &bc, dots, coef);
+        fd += o.fd;
+        negc += o.negcurv;
+    }
+    for (int i = tid; i < N; i += blockDim.x) a.s[i] = coarse_inner(g, i) ? x[i] : T(0);
+    if (tid == 0) {
+        if (a.iters) *a.iters += fd;
+        a.lb->shifts += nshift;
+        a.lb->negcurv += negc;
+    }
+}
+
+size_t coarse_cgqn_smem_bytes(const Grid& g, size_t esz) {
+    const int ne = (g.d == 3) ? g.n * g.n * g.n : g.n * g.n;
+    const int npe = (g.d == 3) ? 8 : 4;
+    size_t b = esz * (7 * (size_t)g.size + (size_t)ne * npe);
+    b = (b + 15) & ~size_t(15);
+    b += sizeof(double) * (4 * kMaxLbfgsPairs + 2 + 32);
+    return b;
+}
+
 template <typename T, Prob P, bool ADJ>
 __global__ void __launch_bounds__(kCoarseThreads) coarse_gmres_kernel(CoarseArgs<T> a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -313,17 +598,50 @@ size_t coarse_smem_bytes(const Grid& g, int maxit) {
 }
 
 template <typename T>
+static jfnk_status launch_coarse_cgqn(Prob prob, const CoarseArgs<T>& a, cudaStream_t st) {
+    if (a.adjoint) {
+        set_error("the CG-QN coarse solver is implemented for the forward operator");
+        return JFNK_ERR_NOT_IMPLEMENTED;
+    }
+    if (!a.lb || !a.S_all || !a.Y_all || !a.S || !a.Y || a.m_pairs < 1 || a.m_pairs > kMaxLbfgsPairs) {
+        set_error("CG-QN coarse solver: workspace not laid out for it, or 1 <= pairs <= %d violated", kMaxLbfgsPairs);
+        return JFNK_ERR_WORKSPACE;
+    }
+    const size_t smem = coarse_cgqn_smem_bytes(a.g, sizeof(T));
+    if (smem > 200 * 1024) {
+        set_error("coarse solver shared memory %zu too large", smem);
+        return JFNK_ERR_INVALID_ARG;
+    }
+#define JFNK_CGQN_LAUNCH(PP)                                                                         \
+    do {                                                                                             \
+        JFNK_CUDA_TRY(cudaFuncSetAttribute(coarse_cgqn_kernel<T, PP>,                                 \
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)); \
+        coarse_cgqn_kernel<T, PP><<<1, kCoarseThreads, smem, st>>>(a);                                \
+    } while (0)
+    switch (prob) {
+        case Prob::BRATU2: JFNK_CGQN_LAUNCH(Prob::BRATU2); break;
+        case Prob::MINSURF2: JFNK_CGQN_LAUNCH(Prob::MINSURF2); break;
+        case Prob::ND3: JFNK_CGQN_LAUNCH(Prob::ND3); break;
+        case Prob::NDK3: JFNK_CGQN_LAUNCH(Prob::NDK3); break;
+    }
+#undef JFNK_CGQN_LAUNCH
+    JFNK_LAUNCH_CHECK();
+    return JFNK_OK;
+}
+
+template <typename T>
 jfnk_status launch_coarse(Prob prob, const CoarseArgs<T>& a, cudaStream_t st) {
     if (a.g.size > JFNK_COARSE_MAX_NODES || a.maxit > JFNK_COARSE_MAX_IT || a.maxit < 1) {
         set_error("coarse grid too large for the single-CTA solver (%lld nodes, maxit %d)", a.g.size, a.maxit);
         return JFNK_ERR_INVALID_ARG;
     }
+    if (a.method == 1) return launch_coarse_cgqn<T>(prob, a, st);
     const size_t smem = coarse_smem_bytes<T>(a.g, a.maxit);
     if (smem > 200 * 1024) {
         set_error("coarse solver shared memory %zu too large", smem);
         return JFNK_ERR_INVALID_ARG;
     }
-    if (a.adjoint && prob == Prob::BRATU2) {
+    if (a.adjoint && is_2d(prob)) {
         set_error("the adjoint coarse solve is implemented for the 3D diffusion problems");
         return JFNK_ERR_NOT_IMPLEMENTED;
     }
@@ -335,6 +653,7 @@ jfnk_status launch_coarse(Prob prob, const CoarseArgs<T>& a, cudaStream_t st) {
     } while (0)
     switch (prob) {
         case Prob::BRATU2: JFNK_COARSE_LAUNCH(Prob::BRATU2, false); break;
+        case Prob::MINSURF2: JFNK_COARSE_LAUNCH(Prob::MINSURF2, false); break;
         case Prob::ND3:
             if (a.adjoint) JFNK_COARSE_LAUNCH(Prob::ND3, true);
             else JFNK_COARSE_LAUNCH(Prob::ND3, false);

@@ -294,4 +294,50 @@ __host__ __device__ __forceinline__ void elem_bratu2(const T u[4], T lh, T r[4])
     r[2] = g0_1 - g1_1; r[3] = g0_1 + g1_1;
 }
 
+// ---------------------------------------------------------------------------
+// 2D minimal-surface element (Sec. 3, "Minimal Surface").
+//   u[4]:   nodal values, index a + 2b
+//   inv_h2: 1/h^2
+//   r[4]:   int_e grad u_h . grad phi_ab / sqrt(1 + |grad u_h|^2)   (exact scale)
+// With the modes M of elem_bratu2, h grad u_h at the Gauss point (sx, sy) is
+//   (M10/2 + sy (A/2) M11,  M01/2 + sx (A/2) M11),
+// the x component depends on sy only and the y component on sx only.  With
+// X_q = c_q Gx_q / 4, Y_q = c_q Gy_q / 4 (c = 1/sqrt(1+|grad u|^2), weights 1/4)
+// the test-function side is r_ab = s_a P1 + s_b P2 + s_a s_b P3 with
+// P1 = sum X / 2, P2 = sum Y / 2, P3 = (A/2)(sum sy X + sum sx Y), s_0 = -1, s_1 = 1.
+// ---------------------------------------------------------------------------
+template <typename T>
+__host__ __device__ __forceinline__ T rsqrt_t(T x);
+template <>
+__host__ __device__ __forceinline__ double rsqrt_t<double>(double x) { return 1.0 / sqrt(x); }
+template <>
+__host__ __device__ __forceinline__ float rsqrt_t<float>(float x) { return 1.0f / sqrtf(x); }
+
+template <typename T>
+__host__ __device__ __forceinline__ void elem_minsurf2(const T u[4], T inv_h2, T r[4]) {
+    const T HA = T(0.28867513459481288225);  // A/2 = 1/(2 sqrt 3)
+    T p0 = u[0] + u[1], q0 = u[1] - u[0];
+    T p1 = u[2] + u[3], q1 = u[3] - u[2];
+    T M10 = q0 + q1, M01 = p1 - p0, M11 = q1 - q0;
+    const T gx0 = T(0.5) * M10, gy0 = T(0.5) * M01, gd = HA * M11;
+    const T gxm = gx0 - gd, gxp = gx0 + gd;  // Gx(sy = -1), Gx(sy = +1)
+    const T gym = gy0 - gd, gyp = gy0 + gd;  // Gy(sx = -1), Gy(sx = +1)
+    const T axm = gxm * gxm, axp = gxp * gxp, aym = gym * gym, ayp = gyp * gyp;
+    // c at (sx, sy)
+    const T cmm = rsqrt_t<T>(T(1) + (axm + aym) * inv_h2);
+    const T cpm = rsqrt_t<T>(T(1) + (axm + ayp) * inv_h2);
+    const T cmp = rsqrt_t<T>(T(1) + (axp + aym) * inv_h2);
+    const T cpp = rsqrt_t<T>(T(1) + (axp + ayp) * inv_h2);
+    // sums over sx of c at fixed sy (x flux) and over sy at fixed sx (y flux), times 1/4
+    const T Xm = T(0.25) * gxm * (cmm + cpm), Xp = T(0.25) * gxp * (cmp + cpp);
+    const T Ym = T(0.25) * gym * (cmm + cmp), Yp = T(0.25) * gyp * (cpm + cpp);
+    const T P1 = T(0.5) * (Xm + Xp);
+    const T P2 = T(0.5) * (Ym + Yp);
+    const T P3 = HA * ((Xp - Xm) + (Yp - Ym));
+    r[0] = P3 - P1 - P2;
+    r[1] = P1 - P2 - P3;
+    r[2] = P2 - P1 - P3;
+    r[3] = P1 + P2 + P3;
+}
+
 }  // namespace jfnk

@@ -31,8 +31,10 @@
 #include "vector.cuh"
 #include "batch.cuh"
 #include "profile.cuh"
+#include "stencil_ep.cuh"
 #include "stencil_v2.cuh"
 #include <algorithm>
+#include <cstdlib>
 
 namespace jfnk {
 
@@ -99,15 +101,21 @@ struct jfnk_problem {
     long long* coarse_iters;
     void* coarseV;
     double* coarseH;
+    // CG-QN coarse solver: collected and kept secant pairs, compact-form state
+    void *cgS_all, *cgY_all, *cgS, *cgY;
+    jfnk::LbfgsState* lb;
     double* mms_tab;
     char* batch = nullptr;  // descriptor staging when this problem leads a batched solve
     size_t batch_bytes = 0;
-    char* face = nullptr;  // face buffer of the halo-free 3D kernel
+    char* face = nullptr;  // scratch of the 3D kernels (face sums / element contributions)
     size_t face_bytes = 0;
+    // 3D levels with n <= ep_max_n run the element-parallel kernels (per precision)
+    int ep_max_n64 = 1 << 20;
+    int ep_max_n32 = 64;
     // captured V-cycle (Lf.b -> Lf.s) and the options it was captured for
     cudaGraphExec_t vgraph = nullptr;
     cudaStream_t cap_stream = nullptr;
-    long long vgraph_key[12] = {0};
+    long long vgraph_key[16] = {0};
     long long vgraph_nF[JFNK_MAX_LEVELS] = {0};
     long long vgraph_launches = 0;
     // host counters
@@ -167,8 +175,14 @@ static size_t plan(P& p, char* base, const jfnk_options* o) {
     }
     const Grid& gf = p.lv[p.L].g;
     const size_t N = (size_t)gf.size;
+    if (const char* e = getenv("JFNK_EP3D_MAX_N_F64")) p.ep_max_n64 = atoi(e);
+    if (const char* e = getenv("JFNK_EP3D_MAX_N_F32")) p.ep_max_n32 = atoi(e);
     long long face = 0;
-    for (int l = 0; l <= p.L; ++l) face = std::max(face, v2_face_count(p.lv[l].g));
+    for (int l = 0; l <= p.L; ++l) {
+        const Grid& g = p.lv[l].g;
+        face = std::max(face, v2_face_count(g));
+        if (g.n <= std::max(p.ep_max_n64, p.ep_max_n32)) face = std::max(face, ep3d_scratch_count(g));
+    }
     p.face_bytes = (size_t)face * sizeof(double);
     p.face = face > 0 ? pl.take<char>(p.face_bytes) : nullptr;
     p.F64 = pl.take<double>(N);
@@ -207,6 +221,11 @@ static size_t plan(P& p, char* base, const jfnk_options* o) {
         const int cm = o->coarse_maxit > 0 ? o->coarse_maxit : (int)g0.interior();
         p.coarseV = pl.take<char>((size_t)(cm + 1) * g0.size * esz_pc);
         p.coarseH = pl.take<double>((size_t)(cm + 1) * cm);
+        p.cgS_all = pl.take<char>((size_t)cm * g0.size * esz_pc);
+        p.cgY_all = pl.take<char>((size_t)cm * g0.size * esz_pc);
+        p.cgS = pl.take<char>((size_t)kMaxLbfgsPairs * g0.size * esz_pc);
+        p.cgY = pl.take<char>((size_t)kMaxLbfgsPairs * g0.size * esz_pc);
+        p.lb = pl.take<LbfgsState>(1);
         // descriptor staging of batched solves led by this problem
         p.batch_bytes = (size_t)32 << 20;
         p.batch = pl.take<char>(p.batch_bytes);
@@ -227,9 +246,15 @@ static EpsParams eps_params(P& p, int l, int mode) {
 static Prob prob_of(const P& p) {
     switch (p.desc.kind) {
         case JFNK_BRATU2D: return Prob::BRATU2;
+        case JFNK_MINSURF2D: return Prob::MINSURF2;
         case JFNK_ND3D: return Prob::ND3;
         default: return Prob::NDK3;
     }
+}
+
+// element parameter of the 2D problems: Bratu lambda h^2 / 16, minimal surface 1 / h^2
+static double lh_of(const P& p, double h) {
+    return p.desc.kind == JFNK_MINSURF2D ? 1.0 / (h * h) : p.desc.lambda * h * h / 16.0;
 }
 
 template <typename T>
@@ -253,7 +278,7 @@ static StencilArgs<T> base_args(P& p, int l) {
     memset(&a, 0, sizeof(a));
     a.g = L.g;
     a.node_scale = (T)(p.d == 3 ? 3.0 * L.h / 16.0 : 1.0);
-    a.lh = (T)(p.desc.lambda * L.h * L.h / 16.0);
+    a.lh = (T)lh_of(p, L.h);
     a.kappa = kappa_of<T>(p, l);
     a.partials = p.red->partial;
     a.counter = &p.red->counter[1];
@@ -261,6 +286,7 @@ static StencilArgs<T> base_args(P& p, int l) {
     a.red = RedOut::NONE;
     a.face = reinterpret_cast<T*>(p.face);
     a.face_cap = (long long)(p.face_bytes / sizeof(T));
+    a.ep_max_n = sizeof(T) == 8 ? p.ep_max_n64 : p.ep_max_n32;
     return a;
 }
 
@@ -353,7 +379,7 @@ static jfnk_status coarse_solve(P& p, const jfnk_options& o, const T* b, T* s, c
     a.b = b;
     a.s = s;
     a.kappa = kappa_of<T>(p, 0);
-    a.lh = (T)(p.desc.lambda * L.h * L.h / 16.0);
+    a.lh = (T)lh_of(p, L.h);
     a.node_scale = (T)(p.d == 3 ? 3.0 * L.h / 16.0 : 1.0);
     a.eps_mode = o.eps_mode_pc;
     a.n_unknowns = (double)L.g.interior();
@@ -365,6 +391,15 @@ static jfnk_status coarse_solve(P& p, const jfnk_options& o, const T* b, T* s, c
     a.H = p.coarseH;
     a.iters = p.coarse_iters;
     a.adjoint = p.adj ? 1 : 0;
+    // the adjoint solve keeps GMRES (its operator J^T is not the Hessian of an energy)
+    a.method = (o.coarse_method == JFNK_COARSE_CGQN && !p.adj) ? 1 : 0;
+    a.m_pairs = o.lbfgs_pairs;
+    a.shift_gamma = o.shift_gamma;
+    a.S_all = as<T>(p.cgS_all);
+    a.Y_all = as<T>(p.cgY_all);
+    a.S = as<T>(p.cgS);
+    a.Y = as<T>(p.cgY);
+    a.lb = p.lb;
     return launch_coarse<T>(prob_of(p), a, st);
 }
 
@@ -404,9 +439,11 @@ static jfnk_status vcycle(P& p, const jfnk_options& o, int l, T* b, T* s, cudaSt
 // is recaptured when the options that shape it change.
 template <typename T>
 static jfnk_status vcycle_graph(P& p, const jfnk_options& o, cudaStream_t st) {
-    long long key[12] = {o.nu_pre, o.nu_post, o.cheb_degree, o.pc_dtype, o.eps_mode_pc, p.coarse_maxit, 0,
-                         o.coarse_tol_mode, p.adj ? 1 : 0, (long long)sizeof(T), 1, 0};
+    long long key[16] = {o.nu_pre, o.nu_post, o.cheb_degree, o.pc_dtype, o.eps_mode_pc, p.coarse_maxit, 0,
+                         o.coarse_tol_mode, p.adj ? 1 : 0, (long long)sizeof(T), 1, o.coarse_method,
+                         o.lbfgs_pairs, 0, 0, 0};
     memcpy(&key[6], &o.coarse_tol, sizeof(double));
+    memcpy(&key[13], &o.shift_gamma, sizeof(double));
     if (p.vgraph && memcmp(key, p.vgraph_key, sizeof(key)) != 0) {
         cudaGraphExecDestroy(p.vgraph);
         p.vgraph = nullptr;
@@ -445,6 +482,14 @@ static jfnk_status vcycle_graph(P& p, const jfnk_options& o, cudaStream_t st) {
 template <typename T>
 static jfnk_status mg_setup_T(P& p, const jfnk_options& o, const double* u, int newton_step, cudaStream_t st) {
     Level& Lf = p.lv[p.L];
+    if (newton_step == 0 && p.lb) {
+        // the L-BFGS preconditioner of the coarse CG is built during the first
+        // coarse solve of a Newton run (Sec. 3) and kept until the next run
+        LbfgsState h;
+        memset(&h, 0, sizeof(h));
+        h.count = -1;
+        JFNK_CUDA_TRY(cudaMemcpyAsync(p.lb, &h, 4 * sizeof(int), cudaMemcpyHostToDevice, st));
+    }
     JFNK_TRY((cast_copy<T, double>(as<T>(Lf.x), u, Lf.g.size, st)));
     for (int l = p.L; l >= 1; --l)
         JFNK_TRY(restrict_to<T>(p.lv[l].g, p.lv[l - 1].g, as<T>(p.lv[l].x), as<T>(p.lv[l - 1].x), true, st));
@@ -661,6 +706,87 @@ static jfnk_status fgmres(P& p, const jfnk_options& o, const double* u, double e
     return JFNK_OK;
 }
 
+// z = MG(r) for the outer Krylov method: r (FP64) -> preconditioner precision
+// -> V-cycle (graph replay when enabled) -> z (FP64)
+template <typename T>
+static jfnk_status apply_mg64(P& p, const jfnk_options& o, const double* r, double* z, cudaStream_t st) {
+    Level& Lf = p.lv[p.L];
+    const long long N = Lf.g.size;
+    JFNK_TRY((cast_copy<T, double>(as<T>(Lf.b), r, N, st)));
+    if (o.use_graph && !prof_on()) {
+        JFNK_TRY(vcycle_graph<T>(p, o, st));
+    } else {
+        JFNK_TRY(vcycle<T>(p, o, p.L, as<T>(Lf.b), as<T>(Lf.s), st));
+    }
+    return cast_copy<double, T>(z, as<T>(Lf.s), N, st);
+}
+
+static jfnk_status dot2(P& p, const double* a, const double* b, const double* c, const double* d, double* out,
+                        cudaStream_t st) {
+    const long long N = p.lv[p.L].g.size;
+    JFNK_TRY(multi_dot(a, b, N, N, 1, p.hbuf, p.dot_partials, &p.counters[2], st));
+    if (c) JFNK_TRY(multi_dot(c, d, N, N, 1, p.hbuf + 1, p.dot_partials, &p.counters[2], st));
+    JFNK_CUDA_TRY(cudaMemcpyAsync(out, p.hbuf, sizeof(double) * (c ? 2 : 1), cudaMemcpyDeviceToHost, st));
+    JFNK_CUDA_TRY(cudaStreamSynchronize(st));
+    return JFNK_OK;
+}
+
+// The paper's outer Krylov method (Sec. 3): preconditioned CG for J delta = -F
+// from delta = 0 with z = MG(r), stopped at ||r|| <= eta ||F|| or max_linear
+// iterations.  On negative curvature p.Jp <= 0 it returns the current iterate,
+// or the first search direction at the first iteration (Nocedal & Wright,
+// Numerical Optimization, Alg. 7.1).  Vectors: delta, r = tmp64, z = z64,
+// p = V64 (the FGMRES basis is unused), q = J p = w64.
+template <typename T>
+static jfnk_status pcg(P& p, const jfnk_options& o, const double* u, double eta, int& its, int& negc,
+                       cudaStream_t st) {
+    const long long N = p.lv[p.L].g.size;
+    double* pd = p.V64;
+    its = 0;
+    negc = 0;
+    JFNK_CUDA_TRY(cudaMemsetAsync(p.delta, 0, sizeof(double) * N, st));
+    JFNK_CUDA_TRY(cudaMemcpyAsync(p.tmp64, p.rhs64, sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
+    double res = 0.0;
+    JFNK_TRY(read_norm(p, p.tmp64, &res, st));
+    if (!(res > 0.0)) return JFNK_OK;
+    if (!std::isfinite(res)) {
+        set_error("non-finite right-hand side in CG");
+        return JFNK_ERR_NONFINITE;
+    }
+    const double target = eta * res;
+    JFNK_TRY(apply_mg64<T>(p, o, p.tmp64, p.z64, st));
+    double rz = 0.0;
+    JFNK_TRY(dot2(p, p.tmp64, p.z64, nullptr, nullptr, &rz, st));
+    JFNK_CUDA_TRY(cudaMemcpyAsync(pd, p.z64, sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
+    for (int it = 1; it <= o.max_linear; ++it) {
+        JFNK_TRY(jv64(p, u, p.Au64, pd, p.w64, st));
+        double pq = 0.0;
+        JFNK_TRY(dot2(p, pd, p.w64, nullptr, nullptr, &pq, st));
+        its = it;
+        if (!std::isfinite(pq)) {
+            set_error("non-finite curvature in CG");
+            return JFNK_ERR_NONFINITE;
+        }
+        if (pq <= 0.0) {
+            negc = 1;
+            if (it == 1) JFNK_CUDA_TRY(cudaMemcpyAsync(p.delta, pd, sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
+            return JFNK_OK;
+        }
+        const double alpha = rz / pq;
+        JFNK_TRY(axpby<double>(p.delta, pd, alpha, 1.0, N, st));
+        JFNK_TRY(axpby<double>(p.tmp64, p.w64, -alpha, 1.0, N, st));
+        JFNK_TRY(read_norm(p, p.tmp64, &res, st));
+        if (res <= target || !std::isfinite(res)) break;
+        JFNK_TRY(apply_mg64<T>(p, o, p.tmp64, p.z64, st));
+        double rz_new = 0.0;
+        JFNK_TRY(dot2(p, p.tmp64, p.z64, nullptr, nullptr, &rz_new, st));
+        const double beta = rz_new / rz;
+        rz = rz_new;
+        JFNK_TRY(axpby<double>(pd, p.z64, 1.0, beta, N, st));
+    }
+    return JFNK_OK;
+}
+
 static jfnk_status check_status(P& p, cudaStream_t st) {
     int s = 0;
     JFNK_CUDA_TRY(cudaMemcpyAsync(&s, p.status, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -704,7 +830,13 @@ static jfnk_status solve_T(P& p, const jfnk_options& o, double* u, jfnk_stats* s
         const double eta = (o.eta_mode == 1) ? std::fmin(o.eta_max, normF) : std::fmin(o.eta_max, normF / F0);
         JFNK_TRY(axpby<double>(p.rhs64, p.F64, -1.0, 0.0, N, st));
         int its = 0;
-        JFNK_TRY(fgmres<T>(p, o, u, eta, its, st));
+        if (o.outer == JFNK_OUTER_CG) {
+            int negc = 0;
+            JFNK_TRY(pcg<T>(p, o, u, eta, its, negc, st));
+            S.outer_negcurv += negc;
+        } else {
+            JFNK_TRY(fgmres<T>(p, o, u, eta, its, st));
+        }
         JFNK_TRY(check_status(p, st));
         S.linear_its += its;
         if (k < JFNK_MAX_HIST) S.lin_hist[k] = its;
@@ -789,6 +921,12 @@ static jfnk_status solve_T(P& p, const jfnk_options& o, double* u, jfnk_stats* s
         S.lambda_max[l] = lam;
     }
     S.ge = ge;
+    if (p.lb) {
+        int hs[4] = {0, 0, 0, 0};
+        JFNK_CUDA_TRY(cudaMemcpy(hs, p.lb, sizeof(hs), cudaMemcpyDeviceToHost));
+        S.coarse_shifts = hs[2];
+        S.coarse_negcurv = hs[3];
+    }
     S.status = result;
     S.solve_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     if (stats) *stats = S;
@@ -800,7 +938,11 @@ static jfnk_status check_opts(const P& p, const jfnk_options* o) {
     if (o->restart < 1 || o->restart > JFNK_MAX_RESTART || o->cheb_degree < 1 ||
         o->cheb_degree > kMaxChebDegree || o->nu_pre < 0 || o->nu_post < 0 || o->power_iters < 1 ||
         !(o->cheb_hi > o->cheb_lo) || !(o->cheb_lo > 0.0) || (o->pc_dtype != JFNK_F32 && o->pc_dtype != JFNK_F64) ||
-        (o->eps_mode_pc != JFNK_EPS_PAPER && o->eps_mode_pc != JFNK_EPS_FP32) || o->max_linear < 1) {
+        (o->eps_mode_pc != JFNK_EPS_PAPER && o->eps_mode_pc != JFNK_EPS_FP32) || o->max_linear < 1 ||
+        (o->outer != JFNK_OUTER_FGMRES && o->outer != JFNK_OUTER_CG) ||
+        (o->coarse_method != JFNK_COARSE_GMRES && o->coarse_method != JFNK_COARSE_CGQN) ||
+        (o->coarse_method == JFNK_COARSE_CGQN && (o->lbfgs_pairs < 1 || o->lbfgs_pairs > kMaxLbfgsPairs ||
+                                                  !(o->shift_gamma > 1.0)))) {
         set_error("invalid options");
         return JFNK_ERR_INVALID_ARG;
     }
@@ -869,6 +1011,29 @@ void jfnk_default_options(jfnk_options* o) {
     o->ls_max = 10;
     o->seed = 0;
     o->use_graph = 1;
+    o->outer = JFNK_OUTER_FGMRES;
+    o->coarse_method = JFNK_COARSE_GMRES;
+    o->lbfgs_pairs = 20;
+    o->shift_gamma = 5.0;
+}
+
+void jfnk_paper_options(jfnk_options* o) {
+    if (!o) return;
+    jfnk_default_options(o);
+    o->nu_pre = 1;
+    o->nu_post = 1;
+    o->cheb_degree = 5;
+    o->cheb_lo = 0.06;
+    o->cheb_hi = 1.2;
+    o->power_iters = 30;
+    o->power_tol = 1e-2;
+    o->rtol_newton = 0.0;
+    o->atol_newton = 1e-6;
+    o->eta_mode = 1;
+    o->outer = JFNK_OUTER_CG;
+    o->coarse_method = JFNK_COARSE_CGQN;
+    o->lbfgs_pairs = 20;
+    o->shift_gamma = 5.0;
 }
 
 jfnk_status jfnk_problem_create(const jfnk_problem_desc* desc, jfnk_problem** out) {
@@ -877,7 +1042,7 @@ jfnk_status jfnk_problem_create(const jfnk_problem_desc* desc, jfnk_problem** ou
         return JFNK_ERR_INVALID_ARG;
     }
     *out = nullptr;
-    if (desc->kind < JFNK_BRATU2D || desc->kind > JFNK_NDK3D) {
+    if (desc->kind < JFNK_BRATU2D || desc->kind > JFNK_MINSURF2D) {
         set_error("unknown problem kind %d", desc->kind);
         return JFNK_ERR_INVALID_ARG;
     }
@@ -894,7 +1059,7 @@ jfnk_status jfnk_problem_create(const jfnk_problem_desc* desc, jfnk_problem** ou
         set_error("NDK3D needs kappa");
         return JFNK_ERR_INVALID_ARG;
     }
-    const int d = desc->kind == JFNK_BRATU2D ? 2 : 3;
+    const int d = (desc->kind == JFNK_BRATU2D || desc->kind == JFNK_MINSURF2D) ? 2 : 3;
     if (d == 3 && (long long)(desc->n_elem + 1) * (desc->n_elem + 1) * (desc->n_elem + 1) > (1LL << 31)) {
         set_error("grid too large");
         return JFNK_ERR_INVALID_ARG;
@@ -1231,7 +1396,7 @@ static jfnk_status vjp_T(P* p, int level, const T* u, const T* w, T* JTw, T* dk,
 jfnk_status jfnk_vjp(jfnk_problem* p, int level, int dtype, const void* u, const void* w, void* JTw,
                      void* dFdkappa_w, void* stream) {
     JFNK_TRY(check_level(p, level, dtype));
-    if (!u || !w || !JTw || p->desc.kind == JFNK_BRATU2D) {
+    if (!u || !w || !JTw || p->d == 2) {
         set_error("jfnk_vjp: null vector or 2D problem (Bratu's J is symmetric: use jfnk_jvp)");
         return JFNK_ERR_INVALID_ARG;
     }
@@ -1315,7 +1480,7 @@ static jfnk_status adjoint_T(P& p, const jfnk_options& o, const double* u, const
 jfnk_status jfnk_adjoint_solve(jfnk_problem* p, const jfnk_options* opts, const double* u, const double* g,
                                double* lambda, double* grad_kappa, double rtol, jfnk_stats* stats, void* stream) {
     JFNK_TRY(need_solver(p, opts));
-    if (!u || !g || !lambda || p->desc.kind == JFNK_BRATU2D || !(rtol > 0.0)) {
+    if (!u || !g || !lambda || p->d == 2 || !(rtol > 0.0)) {
         set_error("jfnk_adjoint_solve: invalid arguments (3D diffusion problems only, rtol > 0)");
         return JFNK_ERR_INVALID_ARG;
     }

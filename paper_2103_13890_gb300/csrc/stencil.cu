@@ -18,6 +18,7 @@
 #include "element.cuh"
 #include "profile.cuh"
 #include "stencil_body.cuh"
+#include "stencil_ep.cuh"
 #include "stencil_v2.cuh"
 #include "reduce.cuh"
 #include "stencil.cuh"
@@ -111,12 +112,12 @@ __global__ void __launch_bounds__(K3_BX* K3_BY) stencil3d_kernel(const StencilAr
 // ---------------------------------------------------------------------------
 // 2D kernel (Bratu), blockDim.x = BX threads, BX-1 output nodes per row segment
 // ---------------------------------------------------------------------------
-template <typename T, Mode M>
+template <typename T, Prob P, Mode M>
 __global__ void __launch_bounds__(512) stencil2d_kernel(const StencilArgs<T> a, int ychunk, int txo) {
     extern __shared__ unsigned char smem_raw[];
     __shared__ double red_sm[32];
     const int y0 = blockIdx.y * ychunk;
-    stencil2d_body<T, M>(a, blockIdx.x * txo, y0, min(y0 + ychunk, a.g.ny), txo, blockIdx.x + gridDim.x * blockIdx.y,
+    stencil2d_body<T, M, P>(a, blockIdx.x * txo, y0, min(y0 + ychunk, a.g.ny), txo, blockIdx.x + gridDim.x * blockIdx.y,
                          gridDim.x * gridDim.y, smem_raw, red_sm);
 }
 
@@ -147,7 +148,7 @@ static jfnk_status launch3(const StencilArgs<T>& a, cudaStream_t st) {
     return JFNK_OK;
 }
 
-template <typename T, Mode M>
+template <typename T, Prob P, Mode M>
 static jfnk_status launch2(const StencilArgs<T>& a, cudaStream_t st) {
     const Grid& g = a.g;
     // row segments of txo nodes: fewest segments with <= 511 nodes each
@@ -161,21 +162,21 @@ static jfnk_status launch2(const StencilArgs<T>& a, cudaStream_t st) {
         return JFNK_ERR_INVALID_ARG;
     }
     size_t smem = sizeof(T) * (2 * (bx + 1) + 4 * bx);
-    stencil2d_kernel<T, M><<<dim3(segs, gy), dim3(bx), smem, st>>>(a, yc, txo);
+    stencil2d_kernel<T, P, M><<<dim3(segs, gy), dim3(bx), smem, st>>>(a, yc, txo);
     JFNK_LAUNCH_CHECK();
     return JFNK_OK;
 }
 
 template <typename T, Prob P>
 static jfnk_status dispatch_mode(Mode mode, const StencilArgs<T>& a, cudaStream_t st) {
-    if (P == Prob::BRATU2) {
+    if constexpr (is_2d(P)) {
         switch (mode) {
-            case Mode::F: return launch2<T, Mode::F>(a, st);
-            case Mode::JV: return launch2<T, Mode::JV>(a, st);
-            case Mode::BMJ: return launch2<T, Mode::BMJ>(a, st);
-            case Mode::CHEB0: return launch2<T, Mode::CHEB0>(a, st);
-            case Mode::CHEB: return launch2<T, Mode::CHEB>(a, st);
-            case Mode::CHEBLAST: return launch2<T, Mode::CHEBLAST>(a, st);
+            case Mode::F: return launch2<T, P, Mode::F>(a, st);
+            case Mode::JV: return launch2<T, P, Mode::JV>(a, st);
+            case Mode::BMJ: return launch2<T, P, Mode::BMJ>(a, st);
+            case Mode::CHEB0: return launch2<T, P, Mode::CHEB0>(a, st);
+            case Mode::CHEB: return launch2<T, P, Mode::CHEB>(a, st);
+            case Mode::CHEBLAST: return launch2<T, P, Mode::CHEBLAST>(a, st);
         }
     } else {
         switch (mode) {
@@ -193,10 +194,12 @@ static jfnk_status dispatch_mode(Mode mode, const StencilArgs<T>& a, cudaStream_
 
 template <typename T>
 static jfnk_status launch_stencil_impl(Prob prob, Mode mode, const StencilArgs<T>& a, cudaStream_t st) {
-    if (prob != Prob::BRATU2 && a.face != nullptr && v2_applicable(a.g))
+    if (!is_2d(prob) && ep3d_use(a)) return launch_ep3d<T>(prob, mode, false, a, st);
+    if (!is_2d(prob) && a.face != nullptr && v2_applicable(a.g))
         return launch_stencil_v2<T>(prob, mode, a, st);
     switch (prob) {
         case Prob::BRATU2: return dispatch_mode<T, Prob::BRATU2>(mode, a, st);
+        case Prob::MINSURF2: return dispatch_mode<T, Prob::MINSURF2>(mode, a, st);
         case Prob::ND3: return dispatch_mode<T, Prob::ND3>(mode, a, st);
         case Prob::NDK3: return dispatch_mode<T, Prob::NDK3>(mode, a, st);
     }
@@ -207,7 +210,7 @@ static jfnk_status launch_stencil_impl(Prob prob, Mode mode, const StencilArgs<T
 template <typename T>
 jfnk_status launch_stencil(Prob prob, Mode mode, const StencilArgs<T>& a, cudaStream_t st) {
     if (!prof_on()) return launch_stencil_impl<T>(prob, mode, a, st);
-    static const char* pn[] = {"bratu2d", "nd3d", "ndk3d"};
+    static const char* pn[] = {"bratu2d", "nd3d", "ndk3d", "minsurf2d"};
     static const char* mn[] = {"F", "JV", "BMJ", "CHEB0", "CHEB", "CHEBLAST"};
     char name[96];
     snprintf(name, sizeof(name), "stencil_%s_%s_%s_n%d", pn[(int)prob], sizeof(T) == 8 ? "f64" : "f32",

@@ -13,7 +13,9 @@ enum class Mode : int {
     CHEBLAST = 5,  // Jd ; r -= Jd ; d' = c1 d + c2 r ; s += d + d'    (last two steps fused)
 };
 
-enum class Prob : int { BRATU2 = 0, ND3 = 1, NDK3 = 2 };
+enum class Prob : int { BRATU2 = 0, ND3 = 1, NDK3 = 2, MINSURF2 = 3 };
+
+__host__ __device__ constexpr bool is_2d(Prob p) { return p == Prob::BRATU2 || p == Prob::MINSURF2; }
 
 // Reduction epilogue: what the last block does with sum of squares of the
 // reduced output (d', s or out): nothing, store the norm, or turn it into the
@@ -61,7 +63,7 @@ struct StencilArgs {
     const ChebTable* cheb; // CHEB*: coefficients for the level (device)
     int cheb_step;       // CHEB*: index i of the step whose direction is v
     T node_scale;        // 3h/16 (3D) or 1 (2D)
-    T lh;                // Bratu: lambda h^2 / 16
+    T lh;                // Bratu: lambda h^2 / 16; minimal surface: 1 / h^2
     // reduction
     RedOut red;
     double* partials;
@@ -70,9 +72,12 @@ struct StencilArgs {
     EpsSlot* red_eps;    // EPS: FD step of the reduced vector
     EpsParams epsp;
     int* status;         // device status word (non-finite eps)
-    // face buffer of the halo-free 3D kernel (nullable: then the tiled kernel runs)
+    // scratch of the 3D kernels (nullable: then the tiled kernel runs): face
+    // partial sums of the halo-free kernel, or the per-element contributions of
+    // the element-parallel kernels, which run for 3D levels with n <= ep_max_n
     T* face;
     long long face_cap;
+    int ep_max_n;
     // adjoint kernel: per-element (dF/dkappa_e)^T v times dk_scale (nullable)
     T* dkout;
     T dk_scale;

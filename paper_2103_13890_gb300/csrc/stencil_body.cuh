@@ -102,6 +102,54 @@ __device__ __forceinline__ void epilogue(const StencilArgs<T>& a, long long idx,
     }
 }
 
+// Epilogue of the adjoint operator: jd = (J^T v)_i at an interior node (0 on
+// the boundary); the same fused modes as `epilogue` with J^T v in place of the
+// FD action.
+template <typename T, Mode M>
+__device__ __forceinline__ void epilogue_adj(const StencilArgs<T>& a, long long idx, bool inner, T jd,
+                                             const ChebK<T>& ck, float& red) {
+    if (M == Mode::JV) {
+        const T o = inner ? jd : T(0);
+        a.out[idx] = o;
+        red += (float)o * (float)o;
+    } else if (M == Mode::BMJ) {
+        const T o = inner ? a.rhs[idx] - jd : T(0);
+        a.out[idx] = o;
+        red += (float)o * (float)o;
+    } else if (M == Mode::CHEB0) {
+        T rr = T(0), dd = T(0);
+        if (inner) {
+            rr = a.rhs[idx] - jd;
+            dd = rr * ck.theta_inv;
+        }
+        a.out[idx] = rr;
+        a.out2[idx] = dd;
+        red += (float)dd * (float)dd;
+    } else if (M == Mode::CHEB) {
+        T rr = T(0), ss = T(0), dn = T(0);
+        if (inner) {
+            const T dc = a.v[idx];
+            rr = a.r[idx] - jd;
+            ss = a.s[idx] + dc;
+            dn = ck.c1 * dc + ck.c2 * rr;
+        }
+        a.r[idx] = rr;
+        a.s[idx] = ss;
+        a.dnew[idx] = dn;
+        red += (float)dn * (float)dn;
+    } else if (M == Mode::CHEBLAST) {
+        T ss = T(0);
+        if (inner) {
+            const T dc = a.v[idx];
+            const T rr = a.r[idx] - jd;
+            const T dn = ck.c1 * dc + ck.c2 * rr;
+            ss = a.s[idx] + dc + dn;
+        }
+        a.s[idx] = ss;
+        red += (float)ss * (float)ss;
+    }
+}
+
 // bid / nb: index of this CTA among the nb CTAs that reduce together (the
 // whole grid, or one instance's CTAs in a batched launch)
 template <typename T>
@@ -142,7 +190,7 @@ __device__ __forceinline__ void stencil_reduce(const StencilArgs<T>& a, float re
 // ---------------------------------------------------------------------------
 // Row segment [x0, x0+txo) of node rows [y0, y1): blockDim.x = BX >= txo + 1
 // threads; smem_raw holds sizeof(T) * (2 (BX+1) + 4 BX) bytes.
-template <typename T, Mode M>
+template <typename T, Mode M, Prob P = Prob::BRATU2>
 __device__ __forceinline__ void stencil2d_body(const StencilArgs<T>& a, int x0, int y0, int y1, int txo,
                                                unsigned int red_bid, unsigned int red_nb, unsigned char* smem_raw,
                                                double* red_sm) {
@@ -192,7 +240,10 @@ __device__ __forceinline__ void stencil2d_body(const StencilArgs<T>& a, int x0, 
             const T* w0 = W + (j & 1) * (BX + 1);
             const T* w1 = W + ((j + 1) & 1) * (BX + 1);
             T ue[4] = {w0[tx], w0[tx + 1], w1[tx], w1[tx + 1]};
-            elem_bratu2<T>(ue, a.lh, r);
+            if (P == Prob::MINSURF2)
+                elem_minsurf2<T>(ue, a.lh, r);
+            else
+                elem_bratu2<T>(ue, a.lh, r);
         } else {
             r[0] = r[1] = r[2] = r[3] = T(0);
         }

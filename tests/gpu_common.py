@@ -25,3 +25,20 @@ def host(t):
 def rel(a, b):
     nb = np.linalg.norm(b)
     return np.linalg.norm(a - b) / (nb if nb > 0 else 1.0)
+
+
+# 3D kernel selection (read when a Problem is created): "ep" runs the
+# element-parallel kernels on every 3D level, "tiled" the halo-free kernel
+# (n a multiple of 32, n >= 64) or the tiled one, "default" the library's choice.
+KERNEL_PATHS = {
+    "default": {},
+    "ep": {"JFNK_EP3D_MAX_N_F64": "100000", "JFNK_EP3D_MAX_N_F32": "100000"},
+    "tiled": {"JFNK_EP3D_MAX_N_F64": "0", "JFNK_EP3D_MAX_N_F32": "0"},
+}
+
+
+def kernel_path(monkeypatch, path):
+    for k in ("JFNK_EP3D_MAX_N_F64", "JFNK_EP3D_MAX_N_F32"):
+        monkeypatch.delenv(k, raising=False)
+    for k, v in KERNEL_PATHS[path].items():
+        monkeypatch.setenv(k, v)

@@ -4,7 +4,7 @@ autograd) against the oracle and against central differences of the loss
 import numpy as np
 import pytest
 
-from gpu_common import dev, host, jf, rel, torch
+from gpu_common import dev, host, jf, kernel_path, rel, torch
 from oracle import adjoint, fem
 from workloads import kappa_field, noise_like, random_direction, random_state_field
 
@@ -18,9 +18,11 @@ def _opts(pc="f64", rtol=1e-11):
                              eps_mode_pc=m.EPS_FP32 if pc == "f32" else m.EPS_PAPER)
 
 
-@pytest.mark.parametrize("kind,n", [("ndk3d", 5), ("ndk3d", 20), ("ndk3d", 37), ("nd3d", 33)])
+@pytest.mark.parametrize("kind,n", [("ndk3d", 5), ("ndk3d", 20), ("ndk3d", 37), ("nd3d", 33), ("ndk3d", 64)])
 @pytest.mark.parametrize("dt", ["f64", "f32"])
-def test_vjp_parity(kind, n, dt):
+@pytest.mark.parametrize("path", ["default", "ep", "tiled"])
+def test_vjp_parity(kind, n, dt, path, monkeypatch):
+    kernel_path(monkeypatch, path)
     tdt = torch.float64 if dt == "f64" else torch.float32
     tol = 1e-12 if dt == "f64" else 1e-5
     kap = np.exp(np.random.default_rng(2).normal(size=(n, n, n))) if kind == "ndk3d" else None
@@ -54,10 +56,11 @@ def _adjoint_case(n, levels, pc="f64"):
     return p, o, kap, u_obs
 
 
-@pytest.mark.parametrize("pc", ["f64", "f32"])
-def test_adjoint_solve_matches_oracle_adjoint(pc):
+@pytest.mark.parametrize("pc,path", [("f64", "default"), ("f32", "default"), ("f64", "tiled")])
+def test_adjoint_solve_matches_oracle_adjoint(pc, path, monkeypatch):
     """At 33^3 nodes: the multigrid-preconditioned GPU adjoint agrees with the
     oracle's adjoint (assembled J^T, sparse direct solve) to 1e-8."""
+    kernel_path(monkeypatch, path)
     n = 32
     p, o, kap, u_obs = _adjoint_case(n, 4, pc)
     u = torch.zeros((n + 1,) * 3, dtype=torch.float64, device="cuda")

@@ -8,7 +8,7 @@ exact linear maps and agree to round-off."""
 import numpy as np
 import pytest
 
-from gpu_common import dev, host, jf, rel, torch
+from gpu_common import dev, host, jf, kernel_path, rel, torch
 from oracle import adjoint, fem, jfnk, transfer
 from workloads import random_direction, random_state_field
 
@@ -100,9 +100,12 @@ def test_setup_projection_operator_and_power_method(kind, n, levels):
             assert rel(pv, lv[l].power_v) <= 1e-5
 
 
-@pytest.mark.parametrize("kind,n,levels", [("bratu2d", 64, 4), ("nd3d", 32, 4), ("nd3d", 64, 5)])
+@pytest.mark.parametrize("kind,n,levels,path", [("bratu2d", 64, 4, "default"), ("nd3d", 32, 4, "default"),
+                                                ("nd3d", 32, 4, "tiled"), ("nd3d", 64, 5, "default"),
+                                                ("nd3d", 64, 5, "tiled")])
 @pytest.mark.parametrize("nu,zero", [(1, True), (3, True), (2, False)])
-def test_chebyshev_smoother_parity(kind, n, levels, nu, zero):
+def test_chebyshev_smoother_parity(kind, n, levels, path, nu, zero, monkeypatch):
+    kernel_path(monkeypatch, path)
     p, o, lv, oo, u = _setup_pair(kind, n, levels)
     l = levels - 1
     d = fem.dim_of(kind)
@@ -131,9 +134,12 @@ def test_coarse_gmres_parity(kind, n, levels):
     assert rel(s, so) <= _fd_tol(so, se, 1e-9)
 
 
-@pytest.mark.parametrize("kind,n,levels", [("bratu2d", 64, 4), ("nd3d", 32, 4), ("nd3d", 16, 2), ("nd3d", 64, 5)])
-def test_vcycle_parity(kind, n, levels):
+@pytest.mark.parametrize("kind,n,levels,path", [("bratu2d", 64, 4, "default"), ("nd3d", 32, 4, "default"),
+                                                ("nd3d", 16, 2, "default"), ("nd3d", 64, 5, "default"),
+                                                ("nd3d", 64, 5, "tiled")])
+def test_vcycle_parity(kind, n, levels, path, monkeypatch):
     """One V-cycle of Alg. 1 with the GPU's lambda_l given to the oracle."""
+    kernel_path(monkeypatch, path)
     kw = dict(nu_pre=2, nu_post=2, cheb_degree=4) if kind == "nd3d" else {}
     p, o, lv, oo, u = _setup_pair(kind, n, levels, **kw)
     for l in range(1, levels):
@@ -181,8 +187,9 @@ def test_solve_bratu_matches_discrete_solution(pc):
     assert st["newton_its"] <= 6
 
 
-@pytest.mark.parametrize("pc", ["f64", "f32"])
-def test_solve_nd_matches_discrete_solution(pc):
+@pytest.mark.parametrize("pc,path", [("f64", "default"), ("f32", "default"), ("f64", "tiled"), ("f32", "ep")])
+def test_solve_nd_matches_discrete_solution(pc, path, monkeypatch):
+    kernel_path(monkeypatch, path)
     n = 32
     o = _opts(rtol_newton=1e-11, nu_pre=2, nu_post=2, cheb_degree=4,
               pc_dtype=jf().F32 if pc == "f32" else jf().F64,

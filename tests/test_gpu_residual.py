@@ -8,7 +8,7 @@ the test computes that bound from the data (c = 64) rather than fixing it."""
 import numpy as np
 import pytest
 
-from gpu_common import dev, host, jf, rel, torch
+from gpu_common import dev, host, jf, kernel_path, rel, torch
 from oracle import fem, jfnk
 from workloads import random_direction, random_state_field
 
@@ -37,15 +37,19 @@ def _kappa(n, seed=3):
 
 # sizes span several 31 x 7 (3D) / row-segment (2D) tiles with ragged tails
 # (3D grids with n a multiple of 32 and n >= 64 take the halo-free kernel with
-# its face fixup; the others the tiled kernel)
+# its face fixup, the others the tiled kernel, unless the element-parallel
+# kernels run: "path" selects)
 CASES = [("bratu2d", 7), ("bratu2d", 64), ("bratu2d", 95), ("bratu2d", 600),
          ("nd3d", 4), ("nd3d", 33), ("nd3d", 40), ("ndk3d", 5), ("ndk3d", 37),
          ("nd3d", 64), ("nd3d", 96), ("ndk3d", 64)]
+PATH_CASES = [(k, n, path) for k, n in CASES for path in ("default", "ep", "tiled")
+              if k != "bratu2d" or path == "default"]
 
 
-@pytest.mark.parametrize("kind,n", CASES)
+@pytest.mark.parametrize("kind,n,path", PATH_CASES)
 @pytest.mark.parametrize("dirichlet", [0.0, 0.3])
-def test_residual_fp64_fp32_parity(kind, n, dirichlet):
+def test_residual_fp64_fp32_parity(kind, n, path, dirichlet, monkeypatch):
+    kernel_path(monkeypatch, path)
     kap = _kappa(n) if kind == "ndk3d" else None
     p = _problem(kind, n, kappa=kap)
     u = _state(kind, n, seed=n, dirichlet=dirichlet)
@@ -58,10 +62,13 @@ def test_residual_fp64_fp32_parity(kind, n, dirichlet):
     assert rel(F32, F_ora) <= 1e-5
 
 
-@pytest.mark.parametrize("kind,n", [("bratu2d", 512), ("nd3d", 128), ("nd3d", 256), ("ndk3d", 128)])
-def test_residual_full_size_sampled(kind, n):
+@pytest.mark.parametrize("kind,n,path", [("bratu2d", 512, "default"), ("nd3d", 128, "default"),
+                                         ("nd3d", 128, "tiled"), ("nd3d", 256, "default"),
+                                         ("ndk3d", 128, "default")])
+def test_residual_full_size_sampled(kind, n, path, monkeypatch):
     """At the configured full sizes: the oracle evaluates F at 60 sampled nodes
     (its own element routine on the 2^d elements around each)."""
+    kernel_path(monkeypatch, path)
     kap = _kappa(n) if kind == "ndk3d" else None
     p = _problem(kind, n, kappa=kap)
     u = _state(kind, n, seed=7)
@@ -87,8 +94,12 @@ def _fd_bound(kind, u, v, kap, load, eps):
     return 64 * EPS64 * np.linalg.norm(A_abs) * 2 ** d / eps
 
 
-@pytest.mark.parametrize("kind,n", [("bratu2d", 64), ("bratu2d", 95), ("nd3d", 33), ("ndk3d", 20), ("nd3d", 64)])
-def test_jvp_fp64_parity(kind, n):
+@pytest.mark.parametrize("kind,n,path", [("bratu2d", 64, "default"), ("bratu2d", 95, "default"),
+                                         ("nd3d", 33, "default"), ("nd3d", 33, "tiled"),
+                                         ("ndk3d", 20, "default"), ("ndk3d", 20, "tiled"),
+                                         ("nd3d", 64, "default"), ("nd3d", 64, "tiled")])
+def test_jvp_fp64_parity(kind, n, path, monkeypatch):
+    kernel_path(monkeypatch, path)
     kap = _kappa(n) if kind == "ndk3d" else None
     load = fem.mms_load(n) if kind == "nd3d" else None
     p = _problem(kind, n, kappa=kap)
@@ -109,10 +120,12 @@ def test_jvp_fp64_parity(kind, n):
     assert rel(Jv, Jex) <= 1e-5
 
 
-@pytest.mark.parametrize("kind,n", [("bratu2d", 64), ("nd3d", 33), ("nd3d", 64)])
-def test_jvp_fp32_parity(kind, n):
+@pytest.mark.parametrize("kind,n,path", [("bratu2d", 64, "default"), ("nd3d", 33, "default"),
+                                         ("nd3d", 33, "tiled"), ("nd3d", 64, "default"), ("nd3d", 64, "ep")])
+def test_jvp_fp32_parity(kind, n, path, monkeypatch):
     """FP32 action with the single-precision step eps = sqrt(2^-23)(1+||u||)/||v||
     against the oracle's FP64 evaluation of the same quotient."""
+    kernel_path(monkeypatch, path)
     load = fem.mms_load(n) if kind == "nd3d" else None
     p = _problem(kind, n)
     u = _state(kind, n, seed=21)
@@ -140,8 +153,9 @@ def test_jvp_explicit_eps_and_zero_direction():
     assert np.all(Jz == 0)
 
 
-@pytest.mark.parametrize("n", [40, 128])
-def test_residual_deterministic(n):
+@pytest.mark.parametrize("n,path", [(40, "default"), (128, "default"), (128, "tiled")])
+def test_residual_deterministic(n, path, monkeypatch):
+    kernel_path(monkeypatch, path)
     p = _problem("nd3d", n)
     ud = dev(_state("nd3d", n, seed=5))
     a = host(p.residual(ud))
