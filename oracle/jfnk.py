@@ -71,7 +71,7 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-from . import fem, transfer
+from . import fem, hyper, transfer
 from .splitmix import start_vector
 
 EPS64 = 2.0 ** -52
@@ -145,6 +145,56 @@ class Level:
     def F(self, x):
         self.ge += 1
         return fem.residual(self.kind, x, self.lam, self.kappa, self.load)
+
+    # transfers to and from the next coarser level (Sec. 2)
+    def restrict(self, r):
+        return transfer.restrict(r)
+
+    def prolong(self, c):
+        return transfer.prolong(c)
+
+    def project(self, x):
+        return transfer.project(x)
+
+
+class HyperLevel(Level):
+    """A level of the hyperelastic beam (Sec. 3): 10m x m x m elements, three
+    displacement components per node, unknowns away from x = 0 and x = 10."""
+
+    def __init__(self, m):
+        self.kind = "hyper3d"
+        self.n = m
+        self.d = 3
+        self.lam = 0.0
+        self.kappa = None
+        self.load = None
+        self.shape = hyper.shape_of(m)
+        self.mask = hyper.unknown_mask(self.shape)
+        self.n_unknowns = int(self.mask.sum())
+        self.ge = 0
+        self.x = None
+        self.Fx = None
+        self.lam_max = None
+        self.power_v = None
+        self.lbfgs = None
+
+    def F(self, x):
+        self.ge += 1
+        return hyper.residual(x)
+
+    def restrict(self, r):
+        return hyper.restrict(r)
+
+    def prolong(self, c):
+        return hyper.prolong(c)
+
+    def project(self, x):
+        return hyper.project(x)
+
+
+def build_hyper_hierarchy(k):
+    """Levels l = 0..k of the beam at refinement level L_k: m_l = 2^l (T_0 = 10 x 1 x 1)."""
+    return [HyperLevel(2 ** l) for l in range(k + 1)]
 
 
 def build_hierarchy(kind, n_finest, n_levels, lam=0.0, kappa=None, load=None):
@@ -485,9 +535,9 @@ def mg_vcycle(levels, l, b, opts):
         s = chebyshev(lv, s, lv.x, lv.Fx, b, opts.nu_pre, opts.cheb_degree, lv.lam_max,
                       opts.cheb_lo, opts.cheb_hi, mode)
         r = np.where(lv.mask, b - fd_jv(lv, lv.x, lv.Fx, s, mode), 0.0)
-        r_c = transfer.restrict(r)
+        r_c = lv.restrict(r)
         c = mg_vcycle(levels, l - 1, r_c, opts)
-        s = s + transfer.prolong(c)
+        s = s + lv.prolong(c)
         s = chebyshev(lv, s, lv.x, lv.Fx, b, opts.nu_post, opts.cheb_degree, lv.lam_max,
                       opts.cheb_lo, opts.cheb_hi, mode)
     else:
@@ -495,8 +545,9 @@ def mg_vcycle(levels, l, b, opts):
         tol_abs = opts.coarse_tol if opts.coarse_tol_mode == "absolute" else None
         apply_A = lambda v: fd_jv(lv, lv.x, lv.Fx, v, mode)  # noqa: E731
         if opts.coarse == "cgqn":
-            s, _ = coarse_cgqn(apply_A, b, lv, opts.coarse_tol, maxit, opts.lbfgs_pairs,
-                               opts.shift_gamma, tol_abs=tol_abs)
+            s, shifts = coarse_cgqn(apply_A, b, lv, opts.coarse_tol, maxit, opts.lbfgs_pairs,
+                                    opts.shift_gamma, tol_abs=tol_abs)
+            lv.shift_calls = getattr(lv, "shift_calls", 0) + len(shifts) - 1
         else:
             s, _, _ = gmres(apply_A, b, lv.mask, opts.coarse_tol, maxit, tol_abs=tol_abs)
     return s
@@ -508,14 +559,14 @@ def setup_levels(levels, u, opts, newton_step):
     L = len(levels) - 1
     levels[L].x = u
     for l in range(L, 0, -1):
-        levels[l - 1].x = transfer.project(levels[l].x)
+        levels[l - 1].x = levels[l].project(levels[l].x)
     for l in range(L + 1):
         lv = levels[l]
         lv.Fx = lv.F(lv.x)
     for l in range(1, L + 1):
         lv = levels[l]
         if newton_step == 0 or lv.power_v is None:
-            v0 = start_vector(lv.shape, opts.seed, l)
+            v0 = start_vector(lv.shape, opts.seed, l, lv.mask)
         else:
             v0 = lv.power_v
         lv.lam_max, lv.power_v = power_method(lv, lv.x, lv.Fx, v0, opts.power_iters,
@@ -528,7 +579,9 @@ def setup_levels(levels, u, opts, newton_step):
 
 def backtrack(F_of, u, du, Fu, slope, c=1e-4, max_steps=10):
     """Backtracking on phi(alpha) = 1/2||F(u + alpha du)||^2 with quadratic and
-    cubic interpolation.  Returns (alpha, F(u + alpha du), ok)."""
+    cubic interpolation.  A trial step whose residual is not finite (e.g. an
+    inverted element of the hyperelastic beam, J <= 0) is cut to 0.1 alpha and
+    not used as an interpolation point.  Returns (alpha, F(u + alpha du), ok)."""
     f0 = 0.5 * float(np.sum(Fu * Fu))
     alpha = 1.0
     prev_alpha = prev_f = None
@@ -537,6 +590,10 @@ def backtrack(F_of, u, du, Fu, slope, c=1e-4, max_steps=10):
         fn = 0.5 * float(np.sum(Fn * Fn))
         if fn <= f0 + c * alpha * slope:
             return alpha, Fn, True
+        if not np.isfinite(fn):
+            prev_alpha = prev_f = None
+            alpha = 0.1 * alpha
+            continue
         if prev_alpha is None:
             t = -slope * alpha * alpha / (2.0 * (fn - f0 - slope * alpha))
         else:

@@ -66,10 +66,15 @@ def sequential(seed, count):
     return out
 
 
-def start_vector(shape, seed, level):
-    """Random power-method start vector on a full node grid of the given shape."""
-    from .fem import boundary_mask
+def start_vector(shape, seed, level, mask=None):
+    """Random power-method start vector on a full node grid of the given shape
+    (counter = flat array index); zero where mask is False (default: the
+    boundary nodes of a scalar grid)."""
     idx = np.arange(int(np.prod(shape)), dtype=np.uint64).reshape(shape)
     v = uniform_pm1(seed, level, idx)
-    v[boundary_mask(shape)] = 0.0
+    if mask is None:
+        from .fem import boundary_mask
+        v[boundary_mask(shape)] = 0.0
+    else:
+        v[~mask] = 0.0
     return v
