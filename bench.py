@@ -247,36 +247,49 @@ def adjoint_extra(jf, torch, n, shape, stream):
 
 def paper_variant_extra(jf, torch, stream):
     """The paper's own solver (outer CG, V(5,5), coarse CG with L-BFGS and the
-    spectral shift, ||F|| < 1e-6) on its two 2D examples, Bratu lambda = 5 and
-    the minimal surface, at the refinement levels L1..L5 of Sec. 3 (25 * 2^k
-    elements per direction, k + 1 levels): Newton and CG iterations, GE and
-    time to solution (CUDA events, one solve after one warm-up)."""
-    import numpy as np
-    rows = []
-    for kind in ("bratu2d", "minsurf2d"):
-        for k in range(1, 6):
-            n = 25 * 2 ** k
-            o = jf.paper_options()
-            p = jf.Problem(kind, n, k + 1, lam=5.0, options=o)
+    spectral shift, ||F|| < 1e-6) on its three examples at the refinement levels
+    of Sec. 3: Bratu lambda = 5 and the minimal surface on 25 * 2^k elements per
+    direction (L1..L5), the Neo-Hookean beam on 10 * 2^k x 2^k x 2^k (L1..L4);
+    k + 1 levels.  Newton and CG iterations, GE, shifted coarse calls and time to
+    solution (CUDA events, one solve after one warm-up)."""
+    import math
+
+    def boundary(kind, n):
+        if kind == "minsurf2d":  # u = x(1-x) on y = 0, 1 and 0 on x = 0, 1 (Sec. 3)
             u0 = torch.zeros((n + 1, n + 1), dtype=torch.float64)
-            if kind == "minsurf2d":  # u = x(1-x) on y = 0, 1 and 0 on x = 0, 1 (Sec. 3)
-                x = torch.as_tensor(np.linspace(0.0, 1.0, n + 1))
-                u0[0, :] = x * (1.0 - x)
-                u0[-1, :] = x * (1.0 - x)
-            u0 = u0.cuda()
-            u = u0.clone()
-            p.solve(u)
-            torch.cuda.synchronize()
-            ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            u.copy_(u0)
-            ea.record(stream)
-            st = p.solve(u)
-            eb.record(stream)
-            torch.cuda.synchronize()
-            rows.append({"problem": kind, "level": f"L{k}", "n_elem": n, "mg_levels": k + 1,
-                         "newton_its": st["newton_its"], "cg_its": st["linear_its"], "ge": round(st["ge"], 1),
-                         "coarse_shifts": st["coarse_shifts"], "converged": st["converged"],
-                         "s": ea.elapsed_time(eb) * 1e-3})
+            x = torch.linspace(0.0, 1.0, n + 1, dtype=torch.float64)
+            u0[0, :] = x * (1.0 - x)
+            u0[-1, :] = x * (1.0 - x)
+            return u0
+        if kind == "beam3d":  # u = 0 at x = 0, the end rotation u2(y, z) at x = 10 (Sec. 3)
+            u0 = torch.zeros((n + 1, n + 1, 10 * n + 1, 3), dtype=torch.float64)
+            t = torch.linspace(0.0, 1.0, n + 1, dtype=torch.float64)
+            z, y = torch.meshgrid(t, t, indexing="ij")
+            c, s = math.cos(math.pi / 6.0), math.sin(math.pi / 6.0)
+            u0[:, :, -1, 1] = 0.5 * (0.5 + (y - 0.5) * c - (z - 0.5) * s - y)
+            u0[:, :, -1, 2] = 0.5 * (0.5 + (y - 0.5) * s + (z - 0.5) * c - z)
+            return u0
+        return torch.zeros((n + 1, n + 1), dtype=torch.float64)
+
+    rows = []
+    cases = [("bratu2d", k, 25 * 2 ** k) for k in range(1, 6)] + \
+            [("minsurf2d", k, 25 * 2 ** k) for k in range(1, 6)] + [("beam3d", k, 2 ** k) for k in range(1, 5)]
+    for kind, k, n in cases:
+        p = jf.Problem(kind, n, k + 1, lam=5.0, options=jf.paper_options())
+        u0 = boundary(kind, n).cuda()
+        u = u0.clone()
+        p.solve(u)
+        torch.cuda.synchronize()
+        ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        u.copy_(u0)
+        ea.record(stream)
+        st = p.solve(u)
+        eb.record(stream)
+        torch.cuda.synchronize()
+        rows.append({"problem": kind, "level": f"L{k}", "n_elem": n, "mg_levels": k + 1,
+                     "newton_its": st["newton_its"], "cg_its": st["linear_its"], "ge": round(st["ge"], 1),
+                     "coarse_shifts": st["coarse_shifts"], "converged": st["converged"],
+                     "s": ea.elapsed_time(eb) * 1e-3})
     return rows
 
 

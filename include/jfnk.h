@@ -57,8 +57,15 @@ typedef enum { JFNK_F32 = 0, JFNK_F64 = 1 } jfnk_dtype;
  *                from u* = sin(pi x) sin(pi y) sin(pi z)
  *  JFNK_NDK3D    F_i = sum_e kappa_e int_e (1+u^2) grad u.grad phi_i - int phi_i
  *  JFNK_MINSURF2D F_i = int grad u.grad phi_i / sqrt(1 + |grad u|^2)  (Sec. 3, minimal
- *                surface; its Dirichlet data x(1-x) / 0 are the boundary entries of u) */
-typedef enum { JFNK_BRATU2D = 0, JFNK_ND3D = 1, JFNK_NDK3D = 2, JFNK_MINSURF2D = 3 } jfnk_kind;
+ *                surface; its Dirichlet data x(1-x) / 0 are the boundary entries of u)
+ *  JFNK_BEAM3D   Neo-Hookean beam (Sec. 3, hyperelasticity): F_a = int P(F) grad phi_a,
+ *                P = mu F + (lam ln J - mu) F^-T, E = 10, nu = 0.3, on (0,10)x(0,1)^2 with
+ *                10 n_elem x n_elem x n_elem cube elements; vectors hold 3 displacement
+ *                components per node (component fastest: shape (n+1, n+1, 10n+1, 3));
+ *                Dirichlet data (u = 0 at x = 0, the end rotation at x = 10) are the
+ *                entries of u on those faces; the other faces are free (their nodes are
+ *                unknowns).  n_elem / 2^(levels-1) >= 1. */
+typedef enum { JFNK_BRATU2D = 0, JFNK_ND3D = 1, JFNK_NDK3D = 2, JFNK_MINSURF2D = 3, JFNK_BEAM3D = 4 } jfnk_kind;
 
 /* Finite-difference step (Sec. 1):
  *  JFNK_EPS_PAPER  eps = (1/(n ||v||_2)) sum_i sqrt(eps_p)(1+|x_i|), eps_p = 2^-52,

@@ -17,8 +17,8 @@ import ctypes
 import torch
 
 from . import _abi
-from ._abi import (BRATU2D, COARSE_CGQN, COARSE_GMRES, EPS_FP32, EPS_PAPER, F32, F64, KINDS,  # noqa: F401
-                   MINSURF2D, ND3D, NDK3D, OUTER_CG, OUTER_FGMRES)
+from ._abi import (BEAM3D, BRATU2D, COARSE_CGQN, COARSE_GMRES, EPS_FP32, EPS_PAPER, F32, F64,  # noqa: F401
+                   KINDS, MINSURF2D, ND3D, NDK3D, OUTER_CG, OUTER_FGMRES)
 
 _LIB = None
 
@@ -97,7 +97,9 @@ def stats_dict(s):
 class Problem:
     """One discretised problem on the current CUDA device with its workspace.
 
-    kind: "bratu2d" | "nd3d" | "ndk3d" | "minsurf2d"; n_elem: finest elements per direction;
+    kind: "bratu2d" | "nd3d" | "ndk3d" | "minsurf2d" | "beam3d"; n_elem: finest
+    elements per direction (beam3d: across the beam, 10 n_elem along it, vectors of
+    shape (n+1, n+1, 10n+1, 3));
     levels: multigrid levels; lam: Bratu lambda; load: optional FP64 finest
     load vector (nd3d); kappa: FP64 per-element coefficient (ndk3d, n_elem^3).
     options: the jfnk_options the workspace is laid out for (None: residual and
@@ -135,6 +137,8 @@ class Problem:
     def shape(self, level=None):
         lv = self.levels - 1 if level is None else level
         m = (self.n >> (self.levels - 1 - lv)) + 1
+        if self.kind == "beam3d":
+            return (m, m, 10 * (m - 1) + 1, 3)
         return (m,) * self.d
 
     def _lv(self, level):

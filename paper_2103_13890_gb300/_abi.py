@@ -12,8 +12,8 @@ OK = 0
 STATUS = {0: "OK", 1: "INVALID_ARG", 2: "CUDA", 3: "NONFINITE", 4: "NOT_CONVERGED", 5: "BREAKDOWN",
           6: "LINESEARCH", 7: "TIMEOUT", 8: "NOT_IMPLEMENTED", 9: "WORKSPACE"}
 F32, F64 = 0, 1
-BRATU2D, ND3D, NDK3D, MINSURF2D = 0, 1, 2, 3
-KINDS = {"bratu2d": BRATU2D, "nd3d": ND3D, "ndk3d": NDK3D, "minsurf2d": MINSURF2D}
+BRATU2D, ND3D, NDK3D, MINSURF2D, BEAM3D = 0, 1, 2, 3, 4
+KINDS = {"bratu2d": BRATU2D, "nd3d": ND3D, "ndk3d": NDK3D, "minsurf2d": MINSURF2D, "beam3d": BEAM3D}
 EPS_PAPER, EPS_FP32 = 0, 1
 RESTRICT, PROLONG_ADD, PROJECT = 0, 1, 2
 OUTER_FGMRES, OUTER_CG = 0, 1

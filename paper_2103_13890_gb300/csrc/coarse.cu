@@ -17,12 +17,44 @@ namespace jfnk {
 
 constexpr int kCoarseThreads = 512;
 
+// element contributions per element: 2^d (scalar) or 24 (beam)
+__host__ __device__ inline int coarse_npe(const Grid& g) { return g.beam ? 24 : (g.d == 3 ? 8 : 4); }
+
 template <typename T, Prob P>
 __device__ void coarse_apply_A(const Grid& g, const T* w, T* elemC, T* out, const T* kappa, T lh, T node_scale) {
-    // elemC: [nelem][2^d];  out: A(w) scaled, full grid (boundary entries untouched)
+    // elemC: [nelem][npe];  out: A(w) scaled, full grid (boundary entries untouched)
     const int n = g.n;
     const int tid = threadIdx.x;
-    if (is_2d(P)) {
+    if (P == Prob::BEAM3) {
+        // lh = 1/h; 10n x n x n elements, 3 components per node
+        const int ex = 10 * n, ne = ex * n * n;
+        for (int e = tid; e < ne; e += blockDim.x) {
+            const int x = e % ex, y = (e / ex) % n, z = e / (ex * n);
+            T ue[24], r[24];
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+                const int node = ((z + (c >> 2)) * g.ny + y + ((c >> 1) & 1)) * g.nx + x + (c & 1);
+#pragma unroll
+                for (int i = 0; i < 3; ++i) ue[3 * c + i] = w[node * 3 + i];
+            }
+            elem_neohooke<T>(ue, lh, r);
+#pragma unroll
+            for (int k = 0; k < 24; ++k) elemC[e * 24 + k] = r[k];
+        }
+        __syncthreads();
+        for (long long k = tid; k < g.size; k += blockDim.x) {
+            const int i = (int)(k % 3);
+            const int node = (int)(k / 3);
+            const int X = node % g.nx, Y = (node / g.nx) % g.ny, Z = node / (g.nx * g.ny);
+            T acc = T(0);
+            for (int c = 0; c < 8; ++c) {
+                const int xe = X - (c & 1), ye = Y - ((c >> 1) & 1), ze = Z - (c >> 2);
+                if (xe < 0 || xe >= ex || ye < 0 || ye >= n || ze < 0 || ze >= n) continue;
+                acc += elemC[((ze * n + ye) * ex + xe) * 24 + 3 * c + i];
+            }
+            out[k] = acc;
+        }
+    } else if (is_2d(P)) {
         const int ne = n * n;
         for (int e = tid; e < ne; e += blockDim.x) {
             const int ex = e % n, ey = e / n;
@@ -129,23 +161,14 @@ __device__ void coarse_apply_vjp(const Grid& g, const T* x, const T* v, T* elemC
     __syncthreads();
 }
 
-__device__ __forceinline__ bool coarse_inner(const Grid& g, long long i) {
-    const int x = (int)(i % g.sy);
-    const int y = (int)((i / g.sy) % g.ny);
-    bool in = x > 0 && x < g.nx - 1 && y > 0 && y < g.ny - 1;
-    if (g.d == 3) {
-        const int z = (int)(i / g.sz);
-        in = in && z > 0 && z < g.nz - 1;
-    }
-    return in;
-}
+__device__ __forceinline__ bool coarse_inner(const Grid& g, long long i) { return grid_unknown(g, i); }
 
 template <typename T, Prob P, bool ADJ>
 __device__ void coarse_gmres_body(const CoarseArgs<T>& a, unsigned char* smem_raw) {
     const Grid g = a.g;
     const int N = (int)g.size;
-    const int ne = (g.d == 3) ? g.n * g.n * g.n : g.n * g.n;
-    const int npe = (g.d == 3) ? 8 : 4;
+    const int ne = (int)g.elements();
+    const int npe = coarse_npe(g);
     const int m = a.maxit;
     T* wv = reinterpret_cast<T*>(smem_raw);  // [N] work vector
     T* xw = wv + N;                          // [N] x + eps v
@@ -511,8 +534,8 @@ __global__ void __launch_bounds__(kCoarseThreads) coarse_cgqn_kernel(CoarseArgs<
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const Grid g = a.g;
     const int N = (int)g.size;
-    const int ne = (g.d == 3) ? g.n * g.n * g.n : g.n * g.n;
-    const int npe = (g.d == 3) ? 8 : 4;
+    const int ne = (int)g.elements();
+    const int npe = coarse_npe(g);
     T* x = reinterpret_cast<T*>(smem_raw);
     T* r = x + N;
     T* z = r + N;
@@ -565,8 +588,8 @@ __global__ void __launch_bounds__(kCoarseThreads) coarse_cgqn_kernel(CoarseArgs<
 }
 
 size_t coarse_cgqn_smem_bytes(const Grid& g, size_t esz) {
-    const int ne = (g.d == 3) ? g.n * g.n * g.n : g.n * g.n;
-    const int npe = (g.d == 3) ? 8 : 4;
+    const int ne = (int)g.elements();
+    const int npe = coarse_npe(g);
     size_t b = esz * (7 * (size_t)g.size + (size_t)ne * npe);
     b = (b + 15) & ~size_t(15);
     b += sizeof(double) * (4 * kMaxLbfgsPairs + 2 + 32);
@@ -589,8 +612,8 @@ __global__ void __launch_bounds__(kCoarseThreads) coarse_gmres_batched_kernel(co
 
 template <typename T>
 size_t coarse_smem_bytes(const Grid& g, int maxit) {
-    const int ne = (g.d == 3) ? g.n * g.n * g.n : g.n * g.n;
-    const int npe = (g.d == 3) ? 8 : 4;
+    const int ne = (int)g.elements();
+    const int npe = coarse_npe(g);
     size_t b = sizeof(T) * (3 * (size_t)g.size + (size_t)ne * npe);
     b = (b + 15) & ~size_t(15);
     b += sizeof(double) * (4 * (size_t)maxit + 2 + 32);
@@ -621,6 +644,7 @@ static jfnk_status launch_coarse_cgqn(Prob prob, const CoarseArgs<T>& a, cudaStr
     switch (prob) {
         case Prob::BRATU2: JFNK_CGQN_LAUNCH(Prob::BRATU2); break;
         case Prob::MINSURF2: JFNK_CGQN_LAUNCH(Prob::MINSURF2); break;
+        case Prob::BEAM3: JFNK_CGQN_LAUNCH(Prob::BEAM3); break;
         case Prob::ND3: JFNK_CGQN_LAUNCH(Prob::ND3); break;
         case Prob::NDK3: JFNK_CGQN_LAUNCH(Prob::NDK3); break;
     }
@@ -654,6 +678,13 @@ jfnk_status launch_coarse(Prob prob, const CoarseArgs<T>& a, cudaStream_t st) {
     switch (prob) {
         case Prob::BRATU2: JFNK_COARSE_LAUNCH(Prob::BRATU2, false); break;
         case Prob::MINSURF2: JFNK_COARSE_LAUNCH(Prob::MINSURF2, false); break;
+        case Prob::BEAM3:
+            if (a.adjoint) {
+                set_error("no adjoint for the beam");
+                return JFNK_ERR_NOT_IMPLEMENTED;
+            }
+            JFNK_COARSE_LAUNCH(Prob::BEAM3, false);
+            break;
         case Prob::ND3:
             if (a.adjoint) JFNK_COARSE_LAUNCH(Prob::ND3, true);
             else JFNK_COARSE_LAUNCH(Prob::ND3, false);

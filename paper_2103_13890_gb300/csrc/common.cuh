@@ -9,13 +9,19 @@
 namespace jfnk {
 
 // Structured node grid of one level: n elements per direction, full node grid
-// including Dirichlet boundary nodes, x fastest, densely packed.
+// including Dirichlet boundary nodes, x fastest, densely packed.  The beam of
+// the hyperelastic problem (beam = 1) has 10n x n x n elements, nc = 3
+// displacement components per node (component fastest), Dirichlet data on the
+// faces x = 0 and x = 10 only: its y and z faces are free, so their nodes are
+// unknowns.
 struct Grid {
     int d;             // 2 or 3
-    int n;             // elements per direction
+    int n;             // elements per direction (beam: lateral, the length has 10 n)
     int nx, ny, nz;    // nodes per direction (nz = 1 in 2D)
-    long long sy, sz;  // strides of y and z in elements
+    long long sy, sz;  // strides of y and z in entries
     long long size;    // number of entries
+    int nc;            // entries per node
+    int beam;          // 1: the hyperelastic beam
 
     static Grid make(int d, int n) {
         Grid g;
@@ -27,13 +33,50 @@ struct Grid {
         g.sy = g.nx;
         g.sz = (long long)g.nx * g.ny;
         g.size = g.sz * g.nz;
+        g.nc = 1;
+        g.beam = 0;
         return g;
     }
-    long long interior() const {
+    static Grid make_beam(int n) {
+        Grid g;
+        g.d = 3;
+        g.n = n;
+        g.nx = 10 * n + 1;
+        g.ny = n + 1;
+        g.nz = n + 1;
+        g.nc = 3;
+        g.beam = 1;
+        g.sy = (long long)g.nx * 3;
+        g.sz = g.sy * g.ny;
+        g.size = g.sz * g.nz;
+        return g;
+    }
+    __host__ __device__ long long elements() const {
+        if (beam) return 10LL * n * n * n;
+        return d == 3 ? (long long)n * n * n : (long long)n * n;
+    }
+    // unknown entries (the n of the FD-step formula, Sec. 1)
+    __host__ __device__ long long interior() const {
+        if (beam) return (long long)(nx - 2) * ny * nz * nc;
         long long m = (long long)(n - 1) * (n - 1);
         return d == 3 ? m * (n - 1) : m;
     }
 };
+
+// True for the entries that are unknowns (not Dirichlet data) of grid g.
+__host__ __device__ __forceinline__ bool grid_unknown(const Grid& g, long long i) {
+    const long long node = g.nc == 1 ? i : i / g.nc;
+    const long long x = node % g.nx;
+    const long long yz = node / g.nx;
+    if (g.beam) return x > 0 && x < g.nx - 1;
+    const long long y = yz % g.ny;
+    bool in = x > 0 && x < g.nx - 1 && y > 0 && y < g.ny - 1;
+    if (g.d == 3) {
+        const long long z = yz / g.ny;
+        in = in && z > 0 && z < g.nz - 1;
+    }
+    return in;
+}
 
 // Error reporting (thread-local message, see jfnk_last_error)
 void set_error(const char* fmt, ...);

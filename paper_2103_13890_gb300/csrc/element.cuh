@@ -340,4 +340,75 @@ __host__ __device__ __forceinline__ void elem_minsurf2(const T u[4], T inv_h2, T
     r[3] = P1 + P2 + P3;
 }
 
+// ---------------------------------------------------------------------------
+// Neo-Hookean hexahedron of the hyperelastic beam (Sec. 3, "Hyperelasticity").
+//   u[3c + i]: displacement component i at corner c = dx + 2 dy + 4 dz
+//   inv_h:     1 / h (cube of side h)
+//   r[3c + i]: int_e P(F) grad phi_c, component i, with the 2x2x2 Gauss rule,
+//              F = I + grad u, J = det F, P = mu F + (lam ln J - mu) F^-T
+//              (the stress of W = mu/2 (I_C - 3) - mu ln J + lam/2 (ln J)^2);
+//              F^-T = cof(F) / J.  J <= 0 gives a non-finite residual.
+// E = 10, nu = 0.3 (Sec. 3): mu = E / (2 (1 + nu)), lam = E nu / ((1 + nu)(1 - 2 nu)).
+// Direct evaluation: the beam grids are small, so no factorisation is used.
+// ---------------------------------------------------------------------------
+constexpr double kBeamMu = 10.0 / (2.0 * 1.3);
+constexpr double kBeamLambda = 10.0 * 0.3 / (1.3 * 0.4);
+
+template <typename T>
+__host__ __device__ __forceinline__ T log_t(T x);
+template <>
+__host__ __device__ __forceinline__ double log_t<double>(double x) { return log(x); }
+template <>
+__host__ __device__ __forceinline__ float log_t<float>(float x) { return logf(x); }
+
+template <typename T>
+__host__ __device__ inline void elem_neohooke(const T u[24], T inv_h, T r[24]) {
+    const T A = T(0.28867513459481288225);  // 1/(2 sqrt 3)
+    const T mu = T(kBeamMu), lam = T(kBeamLambda);
+    const T h = T(1) / inv_h;
+    const T w = T(0.125) * h * h * h;
+#pragma unroll
+    for (int k = 0; k < 24; ++k) r[k] = T(0);
+#pragma unroll 1
+    for (int q = 0; q < 8; ++q) {
+        const T px = (q & 1) ? T(0.5) + A : T(0.5) - A;
+        const T py = (q & 2) ? T(0.5) + A : T(0.5) - A;
+        const T pz = (q & 4) ? T(0.5) + A : T(0.5) - A;
+        T G[3][3] = {{T(0), T(0), T(0)}, {T(0), T(0), T(0)}, {T(0), T(0), T(0)}};
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            const T sx = (c & 1) ? px : T(1) - px, sy = (c & 2) ? py : T(1) - py, sz = (c & 4) ? pz : T(1) - pz;
+            const T gx = ((c & 1) ? inv_h : -inv_h) * sy * sz;
+            const T gy = ((c & 2) ? inv_h : -inv_h) * sx * sz;
+            const T gz = ((c & 4) ? inv_h : -inv_h) * sx * sy;
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                G[i][0] += u[3 * c + i] * gx;
+                G[i][1] += u[3 * c + i] * gy;
+                G[i][2] += u[3 * c + i] * gz;
+            }
+        }
+        const T F00 = T(1) + G[0][0], F01 = G[0][1], F02 = G[0][2];
+        const T F10 = G[1][0], F11 = T(1) + G[1][1], F12 = G[1][2];
+        const T F20 = G[2][0], F21 = G[2][1], F22 = T(1) + G[2][2];
+        const T C00 = F11 * F22 - F12 * F21, C01 = F12 * F20 - F10 * F22, C02 = F10 * F21 - F11 * F20;
+        const T C10 = F02 * F21 - F01 * F22, C11 = F00 * F22 - F02 * F20, C12 = F01 * F20 - F00 * F21;
+        const T C20 = F01 * F12 - F02 * F11, C21 = F02 * F10 - F00 * F12, C22 = F00 * F11 - F01 * F10;
+        const T J = F00 * C00 + F01 * C01 + F02 * C02;
+        const T kc = (lam * log_t<T>(J) - mu) / J;
+        const T P[3][3] = {{mu * F00 + kc * C00, mu * F01 + kc * C01, mu * F02 + kc * C02},
+                           {mu * F10 + kc * C10, mu * F11 + kc * C11, mu * F12 + kc * C12},
+                           {mu * F20 + kc * C20, mu * F21 + kc * C21, mu * F22 + kc * C22}};
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            const T sx = (c & 1) ? px : T(1) - px, sy = (c & 2) ? py : T(1) - py, sz = (c & 4) ? pz : T(1) - pz;
+            const T gx = ((c & 1) ? inv_h : -inv_h) * sy * sz;
+            const T gy = ((c & 2) ? inv_h : -inv_h) * sx * sz;
+            const T gz = ((c & 4) ? inv_h : -inv_h) * sx * sy;
+#pragma unroll
+            for (int i = 0; i < 3; ++i) r[3 * c + i] += w * (P[i][0] * gx + P[i][1] * gy + P[i][2] * gz);
+        }
+    }
+}
+
 }  // namespace jfnk

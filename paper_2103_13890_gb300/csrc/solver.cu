@@ -32,6 +32,7 @@
 #include "batch.cuh"
 #include "profile.cuh"
 #include "stencil_ep.cuh"
+#include "beam.cuh"
 #include "stencil_v2.cuh"
 #include <algorithm>
 #include <cstdlib>
@@ -181,6 +182,7 @@ static size_t plan(P& p, char* base, const jfnk_options* o) {
     for (int l = 0; l <= p.L; ++l) {
         const Grid& g = p.lv[l].g;
         face = std::max(face, v2_face_count(g));
+        face = std::max(face, beam_scratch_count(g));
         if (g.n <= std::max(p.ep_max_n64, p.ep_max_n32)) face = std::max(face, ep3d_scratch_count(g));
     }
     p.face_bytes = (size_t)face * sizeof(double);
@@ -247,14 +249,22 @@ static Prob prob_of(const P& p) {
     switch (p.desc.kind) {
         case JFNK_BRATU2D: return Prob::BRATU2;
         case JFNK_MINSURF2D: return Prob::MINSURF2;
+        case JFNK_BEAM3D: return Prob::BEAM3;
         case JFNK_ND3D: return Prob::ND3;
         default: return Prob::NDK3;
     }
 }
 
-// element parameter of the 2D problems: Bratu lambda h^2 / 16, minimal surface 1 / h^2
+// element parameter: Bratu lambda h^2 / 16, minimal surface 1 / h^2, beam 1 / h
 static double lh_of(const P& p, double h) {
+    if (p.desc.kind == JFNK_BEAM3D) return 1.0 / h;
     return p.desc.kind == JFNK_MINSURF2D ? 1.0 / (h * h) : p.desc.lambda * h * h / 16.0;
+}
+
+// factor applied to the summed element contributions of a node: 3h/16 for the
+// scaled 3D scalar elements, 1 where the element returns the integral itself
+static double node_scale_of(const P& p, double h) {
+    return (p.d == 3 && p.desc.kind != JFNK_BEAM3D) ? 3.0 * h / 16.0 : 1.0;
 }
 
 template <typename T>
@@ -277,7 +287,7 @@ static StencilArgs<T> base_args(P& p, int l) {
     StencilArgs<T> a;
     memset(&a, 0, sizeof(a));
     a.g = L.g;
-    a.node_scale = (T)(p.d == 3 ? 3.0 * L.h / 16.0 : 1.0);
+    a.node_scale = (T)node_scale_of(p, L.h);
     a.lh = (T)lh_of(p, L.h);
     a.kappa = kappa_of<T>(p, l);
     a.partials = p.red->partial;
@@ -380,7 +390,7 @@ static jfnk_status coarse_solve(P& p, const jfnk_options& o, const T* b, T* s, c
     a.s = s;
     a.kappa = kappa_of<T>(p, 0);
     a.lh = (T)lh_of(p, L.h);
-    a.node_scale = (T)(p.d == 3 ? 3.0 * L.h / 16.0 : 1.0);
+    a.node_scale = (T)node_scale_of(p, L.h);
     a.eps_mode = o.eps_mode_pc;
     a.n_unknowns = (double)L.g.interior();
     a.xstat = (o.eps_mode_pc == JFNK_EPS_PAPER) ? L.xstat_paper : L.xstat_fp32;
@@ -507,10 +517,46 @@ static jfnk_status mg_setup_T(P& p, const jfnk_options& o, const double* u, int 
         Level& L = p.lv[l];
         const EpsParams ep = eps_params(p, l, o.eps_mode_pc);
         if (newton_step == 0 || !L.pv_valid) JFNK_TRY(splitmix_start<T>(L.g, as<T>(L.pv), o.seed, l, st));
-        // normalise the start vector
+        double lam_prev = 0.0;
+        if (!p.adj) {
+            // FD power iteration along unit vectors without normalisation passes:
+            // each action takes v/||v|| (RedOut::EPS_UNIT), so lambda = ||J v/||v|| ||
+            // is the action's own output norm and the output is the next v
+            EpsParams epu = ep;
+            epu.unit = 1;
+            JFNK_TRY(norm_to_eps<T>(L.g, as<T>(L.pv), epu, L.eps_aux, L.nrm0, p.red, st));
+            for (int it = 0; it < o.power_iters; ++it) {
+                StencilArgs<T> a = base_args<T>(p, l);
+                a.u = as<T>(L.x);
+                a.v = as<T>(L.pv);
+                a.eps = L.eps_aux;
+                a.Au = as<T>(L.Ax);
+                a.out = as<T>(L.pw);
+                a.red = RedOut::EPS_UNIT;
+                a.red_norm = L.lam;
+                a.red_eps = L.eps_aux;
+                a.epsp = epu;
+                JFNK_TRY(launch_stencil<T>(prob_of(p), Mode::JV, a, st));
+                p.nF[l]++;
+                void* t = L.pv;
+                L.pv = L.pw;
+                L.pw = t;
+                if (o.power_tol > 0.0) {
+                    double lam = 0.0;
+                    JFNK_CUDA_TRY(cudaMemcpyAsync(&lam, L.lam, sizeof(double), cudaMemcpyDeviceToHost, st));
+                    JFNK_CUDA_TRY(cudaStreamSynchronize(st));
+                    const bool done = it > 0 && std::fabs(lam - lam_prev) < o.power_tol * lam;
+                    lam_prev = lam;
+                    if (done) break;
+                }
+            }
+            L.pv_valid = true;
+            JFNK_TRY(cheb_table(L.lam, o.cheb_lo, o.cheb_hi, o.cheb_degree, L.cheb, p.status, st));
+            continue;
+        }
+        // adjoint operator (exact J^T v): normalise explicitly
         JFNK_TRY(norm_to_eps<T>(L.g, as<T>(L.pv), ep, L.eps_aux, L.nrm0, p.red, st));
         JFNK_TRY(scale_inplace_inv<T>(as<T>(L.pv), L.g.size, L.nrm0, st));
-        double lam_prev = 0.0;
         for (int it = 0; it < o.power_iters; ++it) {
             JFNK_TRY(norm_to_eps<T>(L.g, as<T>(L.pv), ep, L.eps_aux, L.nrm0, p.red, st));
             StencilArgs<T> a = base_args<T>(p, l);
@@ -862,7 +908,10 @@ static jfnk_status solve_T(P& p, const jfnk_options& o, double* u, jfnk_stats* s
                 }
                 double t;
                 if (!std::isfinite(fn)) {
-                    t = 0.1 * alpha;
+                    // cut the step; the trial is not an interpolation point
+                    alpha = 0.1 * alpha;
+                    prev_a = -1.0;
+                    continue;
                 } else if (prev_a < 0.0) {
                     t = -slope * alpha * alpha / (2.0 * (fn - f0 - slope * alpha));
                 } else {
@@ -1042,17 +1091,19 @@ jfnk_status jfnk_problem_create(const jfnk_problem_desc* desc, jfnk_problem** ou
         return JFNK_ERR_INVALID_ARG;
     }
     *out = nullptr;
-    if (desc->kind < JFNK_BRATU2D || desc->kind > JFNK_MINSURF2D) {
+    if (desc->kind < JFNK_BRATU2D || desc->kind > JFNK_BEAM3D) {
         set_error("unknown problem kind %d", desc->kind);
         return JFNK_ERR_INVALID_ARG;
     }
-    if (desc->levels < 1 || desc->levels > JFNK_MAX_LEVELS || desc->n_elem < 2) {
+    if (desc->levels < 1 || desc->levels > JFNK_MAX_LEVELS || desc->n_elem < 1) {
         set_error("invalid levels %d / n_elem %d", desc->levels, desc->n_elem);
         return JFNK_ERR_INVALID_ARG;
     }
     const int L = desc->levels - 1;
-    if ((desc->n_elem >> L) < 2 || ((desc->n_elem >> L) << L) != desc->n_elem) {
-        set_error("n_elem %d is not divisible into %d levels with >= 2 coarse elements", desc->n_elem, desc->levels);
+    const int min_coarse = desc->kind == JFNK_BEAM3D ? 1 : 2;
+    if ((desc->n_elem >> L) < min_coarse || ((desc->n_elem >> L) << L) != desc->n_elem) {
+        set_error("n_elem %d is not divisible into %d levels with >= %d coarse elements", desc->n_elem, desc->levels,
+                  min_coarse);
         return JFNK_ERR_INVALID_ARG;
     }
     if (desc->kind == JFNK_NDK3D && !desc->kappa) {
@@ -1060,7 +1111,8 @@ jfnk_status jfnk_problem_create(const jfnk_problem_desc* desc, jfnk_problem** ou
         return JFNK_ERR_INVALID_ARG;
     }
     const int d = (desc->kind == JFNK_BRATU2D || desc->kind == JFNK_MINSURF2D) ? 2 : 3;
-    if (d == 3 && (long long)(desc->n_elem + 1) * (desc->n_elem + 1) * (desc->n_elem + 1) > (1LL << 31)) {
+    const long long len_mult = desc->kind == JFNK_BEAM3D ? 30 : 1;  // 10x the nodes, 3 components
+    if (d == 3 && (long long)(desc->n_elem + 1) * (desc->n_elem + 1) * (desc->n_elem + 1) * len_mult > (1LL << 31)) {
         set_error("grid too large");
         return JFNK_ERR_INVALID_ARG;
     }
@@ -1072,7 +1124,8 @@ jfnk_status jfnk_problem_create(const jfnk_problem_desc* desc, jfnk_problem** ou
     cudaGetDevice(&p->device);
     p->lv.resize(L + 1);
     for (int l = 0; l <= L; ++l) {
-        p->lv[l].g = Grid::make(d, desc->n_elem >> (L - l));
+        const int nl = desc->n_elem >> (L - l);
+        p->lv[l].g = desc->kind == JFNK_BEAM3D ? Grid::make_beam(nl) : Grid::make(d, nl);
         p->lv[l].h = 1.0 / (double)(desc->n_elem >> (L - l));
         p->lv[l].pv_valid = false;
     }
@@ -1396,7 +1449,7 @@ static jfnk_status vjp_T(P* p, int level, const T* u, const T* w, T* JTw, T* dk,
 jfnk_status jfnk_vjp(jfnk_problem* p, int level, int dtype, const void* u, const void* w, void* JTw,
                      void* dFdkappa_w, void* stream) {
     JFNK_TRY(check_level(p, level, dtype));
-    if (!u || !w || !JTw || p->d == 2) {
+    if (!u || !w || !JTw || p->d == 2 || p->desc.kind == JFNK_BEAM3D) {
         set_error("jfnk_vjp: null vector or 2D problem (Bratu's J is symmetric: use jfnk_jvp)");
         return JFNK_ERR_INVALID_ARG;
     }
@@ -1480,7 +1533,7 @@ static jfnk_status adjoint_T(P& p, const jfnk_options& o, const double* u, const
 jfnk_status jfnk_adjoint_solve(jfnk_problem* p, const jfnk_options* opts, const double* u, const double* g,
                                double* lambda, double* grad_kappa, double rtol, jfnk_stats* stats, void* stream) {
     JFNK_TRY(need_solver(p, opts));
-    if (!u || !g || !lambda || p->d == 2 || !(rtol > 0.0)) {
+    if (!u || !g || !lambda || p->d == 2 || p->desc.kind == JFNK_BEAM3D || !(rtol > 0.0)) {
         set_error("jfnk_adjoint_solve: invalid arguments (3D diffusion problems only, rtol > 0)");
         return JFNK_ERR_INVALID_ARG;
     }

@@ -19,6 +19,7 @@
 #include "profile.cuh"
 #include "stencil_body.cuh"
 #include "stencil_ep.cuh"
+#include "beam.cuh"
 #include "stencil_v2.cuh"
 #include "reduce.cuh"
 #include "stencil.cuh"
@@ -194,12 +195,14 @@ static jfnk_status dispatch_mode(Mode mode, const StencilArgs<T>& a, cudaStream_
 
 template <typename T>
 static jfnk_status launch_stencil_impl(Prob prob, Mode mode, const StencilArgs<T>& a, cudaStream_t st) {
+    if (prob == Prob::BEAM3) return launch_beam<T>(mode, a, st);
     if (!is_2d(prob) && ep3d_use(a)) return launch_ep3d<T>(prob, mode, false, a, st);
     if (!is_2d(prob) && a.face != nullptr && v2_applicable(a.g))
         return launch_stencil_v2<T>(prob, mode, a, st);
     switch (prob) {
         case Prob::BRATU2: return dispatch_mode<T, Prob::BRATU2>(mode, a, st);
         case Prob::MINSURF2: return dispatch_mode<T, Prob::MINSURF2>(mode, a, st);
+        case Prob::BEAM3: break;
         case Prob::ND3: return dispatch_mode<T, Prob::ND3>(mode, a, st);
         case Prob::NDK3: return dispatch_mode<T, Prob::NDK3>(mode, a, st);
     }
@@ -210,12 +213,12 @@ static jfnk_status launch_stencil_impl(Prob prob, Mode mode, const StencilArgs<T
 template <typename T>
 jfnk_status launch_stencil(Prob prob, Mode mode, const StencilArgs<T>& a, cudaStream_t st) {
     if (!prof_on()) return launch_stencil_impl<T>(prob, mode, a, st);
-    static const char* pn[] = {"bratu2d", "nd3d", "ndk3d", "minsurf2d"};
+    static const char* pn[] = {"bratu2d", "nd3d", "ndk3d", "minsurf2d", "beam3d"};
     static const char* mn[] = {"F", "JV", "BMJ", "CHEB0", "CHEB", "CHEBLAST"};
     char name[96];
     snprintf(name, sizeof(name), "stencil_%s_%s_%s_n%d", pn[(int)prob], sizeof(T) == 8 ? "f64" : "f32",
              mn[(int)mode], a.g.n);
-    const double elems = (a.g.d == 3) ? (double)a.g.n * a.g.n * a.g.n : (double)a.g.n * a.g.n;
+    const double elems = (double)a.g.elements();
     prof_begin(name, elems, st);
     jfnk_status s = launch_stencil_impl<T>(prob, mode, a, st);
     prof_end(st);

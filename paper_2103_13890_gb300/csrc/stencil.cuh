@@ -13,14 +13,17 @@ enum class Mode : int {
     CHEBLAST = 5,  // Jd ; r -= Jd ; d' = c1 d + c2 r ; s += d + d'    (last two steps fused)
 };
 
-enum class Prob : int { BRATU2 = 0, ND3 = 1, NDK3 = 2, MINSURF2 = 3 };
+enum class Prob : int { BRATU2 = 0, ND3 = 1, NDK3 = 2, MINSURF2 = 3, BEAM3 = 4 };
 
 __host__ __device__ constexpr bool is_2d(Prob p) { return p == Prob::BRATU2 || p == Prob::MINSURF2; }
 
 // Reduction epilogue: what the last block does with sum of squares of the
 // reduced output (d', s or out): nothing, store the norm, or turn it into the
 // FD step eps of the next action (Sec. 1 formula, mode below).
-enum class RedOut : int { NONE = 0, NORM = 1, EPS = 2 };
+// EPS_UNIT: the next action is taken along the unit vector v/||v|| (power method):
+// the step e of the slot still multiplies v while staging, and the quotient is
+// divided by e ||v||, so the action returns J (v/||v||) without a normalisation pass.
+enum class RedOut : int { NONE = 0, NORM = 1, EPS = 2, EPS_UNIT = 3 };
 
 // FD step of one action, in both precisions, with its reciprocal (computed
 // once by the producer of ||v|| so no kernel divides per thread).
@@ -42,6 +45,7 @@ struct EpsParams {
     int mode;            // JFNK_EPS_PAPER / JFNK_EPS_FP32
     double n_unknowns;   // interior unknowns of the level
     const double* xstat; // device: sum|x_i| (paper) or ||x||_2 (fp32)
+    int unit = 0;        // 1: slots produced from a norm are for the unit direction (EPS_UNIT)
 };
 
 template <typename T>
@@ -63,7 +67,7 @@ struct StencilArgs {
     const ChebTable* cheb; // CHEB*: coefficients for the level (device)
     int cheb_step;       // CHEB*: index i of the step whose direction is v
     T node_scale;        // 3h/16 (3D) or 1 (2D)
-    T lh;                // Bratu: lambda h^2 / 16; minimal surface: 1 / h^2
+    T lh;                // Bratu: lambda h^2 / 16; minimal surface: 1 / h^2; beam: 1 / h
     // reduction
     RedOut red;
     double* partials;
@@ -117,5 +121,24 @@ __host__ __device__ inline double eps_formula(int mode, double n, double xstat, 
     const double sq32 = 3.4526698300124393e-04;    // sqrt(2^-23)
     return sq32 * (1.0 + xstat) / vnorm;
 }
+
+#ifdef __CUDACC__
+// The FD-step slot of the action on a vector of norm nrm (Sec. 1 formula), with
+// its reciprocal in both precisions; unit: for the direction v/||v|| (see
+// RedOut::EPS_UNIT).  A non-finite step sets bit 1 of the status word and 0.
+__device__ inline void set_eps_slot(EpsSlot* slot, const EpsParams& ep, double nrm, bool unit, int* status) {
+    double e = eps_formula(ep.mode, ep.n_unknowns, *ep.xstat, nrm);
+    double inv = e > 0.0 ? 1.0 / (unit ? e * nrm : e) : 0.0;
+    if (!isfinite(e) || !isfinite(inv)) {
+        if (status) atomicOr(status, 1);
+        e = 0.0;
+        inv = 0.0;
+    }
+    slot->e = e;
+    slot->inv = inv;
+    slot->ef = (float)e;
+    slot->invf = (float)inv;
+}
+#endif
 
 }  // namespace jfnk

@@ -162,19 +162,8 @@ __device__ __forceinline__ void stencil_reduce(const StencilArgs<T>& a, float re
         if (threadIdx.x == 0 && threadIdx.y == 0) {
             double nrm = sqrt(tot);
             if (a.red_norm) *a.red_norm = nrm;
-            if (a.red == RedOut::EPS) {
-                double e = eps_formula(a.epsp.mode, a.epsp.n_unknowns, *a.epsp.xstat, nrm);
-                double inv = e > 0.0 ? 1.0 / e : 0.0;
-                if (!isfinite(e) || !isfinite(inv)) {
-                    if (a.status) atomicOr(a.status, 1);
-                    e = 0.0;
-                    inv = 0.0;
-                }
-                a.red_eps->e = e;
-                a.red_eps->inv = inv;
-                a.red_eps->ef = (float)e;
-                a.red_eps->invf = (float)inv;
-            }
+            if (a.red == RedOut::EPS || a.red == RedOut::EPS_UNIT)
+                set_eps_slot(a.red_eps, a.epsp, nrm, a.red == RedOut::EPS_UNIT, a.status);
         }
     }
 }

@@ -25,87 +25,110 @@
 namespace jfnk {
 
 constexpr int kEpElemThreads = 128;
-constexpr int kEpNodeThreads = 256;
+constexpr int kEpNodeThreads = 128;
 
+// Element (x, y, z): blockIdx.y = y, blockIdx.z = z, x = blockIdx.x * blockDim.x
+// + threadIdx.x, so a warp holds consecutive elements of one x-row.  Each
+// thread forms w = x + eps v at its 4 left corners (x, y+dy, z+dz) and takes the
+// 4 right corners from its neighbour lane (the left corners of element x+1);
+// the last element of a row and lane 31 form theirs themselves.  32-bit node
+// indices: (n+1)^3 < 2^31 for every grid the launcher accepts.
 template <typename T, Prob P, Mode M, bool ADJ>
 __global__ void __launch_bounds__(kEpElemThreads) ep3d_elem_kernel(const StencilArgs<T> a) {
-    const Grid g = a.g;
-    const int n = g.n;
+    const int n = a.g.n;
+    const int sy = (int)a.g.sy, sz = (int)a.g.sz;
     const long long ne = (long long)n * n * n;
-    T* C = a.face;
+    const int y = blockIdx.y, z = blockIdx.z;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    const bool valid = x < n;
     T eps = T(0);
     if (!ADJ && M != Mode::F) eps = eps_of<T>(a.eps);
-    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < ne;
-         e += (long long)gridDim.x * blockDim.x) {
-        const int x = (int)(e % n);
-        const long long q = e / n;
-        const int y = (int)(q % n), z = (int)(q / n);
-        const long long base = (long long)z * g.sz + (long long)y * g.sy + x;
-        T ue[8], ve[8];
-#pragma unroll
-        for (int c = 0; c < 8; ++c) {
-            const int dx = c & 1, dy = (c >> 1) & 1, dz = c >> 2;
-            const long long idx = base + dx + dy * g.sy + dz * g.sz;
-            const int X = x + dx, Y = y + dy, Z = z + dz;
-            const bool bnd = X == 0 || X == n || Y == 0 || Y == n || Z == 0 || Z == n;
-            T uv = a.u[idx];
-            if (ADJ) {
-                ve[c] = bnd ? T(0) : a.v[idx];
-            } else if (M != Mode::F) {
-                if (!bnd) uv += eps * a.v[idx];
-            }
-            ue[c] = uv;
-        }
-        T r[8];
+    const bool yz_in0 = y > 0, yz_in1 = y + 1 < n, z_in0 = z > 0, z_in1 = z + 1 < n;
+    // node value (w, or u with the masked direction in vv for the adjoint) at (X, y+dy, z+dz)
+    auto corner = [&](int X, int dy, int dz, T& wv, T& vv) {
+        const int idx = (z + dz) * sz + (y + dy) * sy + X;
+        const bool bnd = X == 0 || X == n || (dy ? !yz_in1 : !yz_in0) || (dz ? !z_in1 : !z_in0);
+        T uv = a.u[idx];
+        vv = T(0);
         if (ADJ) {
-            T dk;
-            elem_vjp3<T>(ue, ve, P == Prob::NDK3 ? a.kappa[e] : T(1), r, dk);
-            if (a.dkout) a.dkout[e] = dk * a.dk_scale;
-        } else if (P == Prob::NDK3) {
-            elem_nd3<T, true>(ue, a.kappa[e], r);
-        } else {
-            elem_nd3<T, false>(ue, T(1), r);
+            vv = bnd ? T(0) : a.v[idx];
+        } else if (M != Mode::F) {
+            if (!bnd) uv += eps * a.v[idx];
         }
+        wv = uv;
+    };
+    const int xl = valid ? x : n - 1;  // inactive lanes still take part in the shuffles
+    T wl[4], vl[4], wr[4], vr[4];
 #pragma unroll
-        for (int c = 0; c < 8; ++c) C[c * ne + e] = r[c];
+    for (int k = 0; k < 4; ++k) corner(xl, k & 1, k >> 1, wl[k], vl[k]);
+    const bool own_right = (lane == 31) || (xl == n - 1);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        wr[k] = __shfl_down_sync(0xffffffffu, wl[k], 1);
+        if (ADJ) vr[k] = __shfl_down_sync(0xffffffffu, vl[k], 1);
     }
+    if (own_right) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) corner(xl + 1, k & 1, k >> 1, wr[k], vr[k]);
+    }
+    if (!valid) return;
+    const long long e = ((long long)z * n + y) * n + x;
+    // corner c = dx + 2 dy + 4 dz
+    T ue[8] = {wl[0], wr[0], wl[1], wr[1], wl[2], wr[2], wl[3], wr[3]};
+    T r[8];
+    if (ADJ) {
+        T ve[8] = {vl[0], vr[0], vl[1], vr[1], vl[2], vr[2], vl[3], vr[3]};
+        T dk;
+        elem_vjp3<T>(ue, ve, P == Prob::NDK3 ? a.kappa[e] : T(1), r, dk);
+        if (a.dkout) a.dkout[e] = dk * a.dk_scale;
+    } else if (P == Prob::NDK3) {
+        elem_nd3<T, true>(ue, a.kappa[e], r);
+    } else {
+        elem_nd3<T, false>(ue, T(1), r);
+    }
+    T* C = a.face + e;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) C[c * ne] = r[c];
 }
 
+// Node rows (Y, Z) grid-strided over the blocks (the last-block reduction holds
+// at most 2 kMaxRedBlocks partials), X over the threads of the block.
 template <typename T, Mode M, bool ADJ>
 __global__ void __launch_bounds__(kEpNodeThreads) ep3d_node_kernel(const StencilArgs<T> a) {
     __shared__ double red_sm[32];
     const Grid g = a.g;
     const int n = g.n, NP = n + 1;
     const long long ne = (long long)n * n * n;
-    const long long nn = (long long)NP * NP * NP;
-    const long long sy = n, sz = (long long)n * n;  // element strides
+    const int sy = (int)g.sy, sz = (int)g.sz;
+    const int esy = n, esz = n * n;  // element strides
     const T* C = a.face;
     T inv_eps = T(0);
     if (!ADJ && M != Mode::F) inv_eps = inv_eps_of<T>(a.eps);
     ChebK<T> ck = {T(0), T(0), T(0)};
     if (M == Mode::CHEB0 || M == Mode::CHEB || M == Mode::CHEBLAST) ck = cheb_of<T>(a.cheb, a.cheb_step);
     float red = 0.f;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nn;
-         i += (long long)gridDim.x * blockDim.x) {
-        const int X = (int)(i % NP);
-        const long long q = i / NP;
-        const int Y = (int)(q % NP), Z = (int)(q / NP);
-        const long long idx = (long long)Z * g.sz + (long long)Y * g.sy + X;
-        const bool inner = X > 0 && X < n && Y > 0 && Y < n && Z > 0 && Z < n;
-        T val = T(0);
-        if (inner) {
-            // element with corner c = dx + 2 dy + 4 dz at this node: (X-dx, Y-dy, Z-dz)
-            const long long e0 = (long long)Z * sz + (long long)Y * sy + X;
-            const T c0 = C[0 * ne + e0], c1 = C[1 * ne + e0 - 1];
-            const T c2 = C[2 * ne + e0 - sy], c3 = C[3 * ne + e0 - sy - 1];
-            const T c4 = C[4 * ne + e0 - sz], c5 = C[5 * ne + e0 - sz - 1];
-            const T c6 = C[6 * ne + e0 - sz - sy], c7 = C[7 * ne + e0 - sz - sy - 1];
-            val = (((c0 + c1) + (c2 + c3)) + ((c4 + c5) + (c6 + c7))) * a.node_scale;
+    for (int row = blockIdx.x; row < NP * NP; row += gridDim.x) {
+        const int Y = row % NP, Z = row / NP;
+        const bool yz_inner = Y > 0 && Y < n && Z > 0 && Z < n;
+        for (int X = threadIdx.x; X < NP; X += blockDim.x) {
+            const int idx = Z * sz + Y * sy + X;
+            const bool inner = yz_inner && X > 0 && X < n;
+            T val = T(0);
+            if (inner) {
+                // element with corner c = dx + 2 dy + 4 dz at this node: (X-dx, Y-dy, Z-dz)
+                const T* Cn = C + (Z * esz + Y * esy + X);
+                const T c0 = Cn[0], c1 = Cn[ne - 1];
+                const T c2 = Cn[2 * ne - esy], c3 = Cn[3 * ne - esy - 1];
+                const T c4 = Cn[4 * ne - esz], c5 = Cn[5 * ne - esz - 1];
+                const T c6 = Cn[6 * ne - esz - esy], c7 = Cn[7 * ne - esz - esy - 1];
+                val = (((c0 + c1) + (c2 + c3)) + ((c4 + c5) + (c6 + c7))) * a.node_scale;
+            }
+            if (ADJ)
+                epilogue_adj<T, M>(a, idx, inner, val, ck, red);
+            else
+                epilogue<T, M>(a, idx, inner, val, inv_eps, ck, red);
         }
-        if (ADJ)
-            epilogue_adj<T, M>(a, idx, inner, val, ck, red);
-        else
-            epilogue<T, M>(a, idx, inner, val, inv_eps, ck, red);
     }
     stencil_reduce(a, red, red_sm);
 }
@@ -113,18 +136,22 @@ __global__ void __launch_bounds__(kEpNodeThreads) ep3d_node_kernel(const Stencil
 template <typename T, Prob P, Mode M, bool ADJ>
 static jfnk_status launch_ep3d_pm(const StencilArgs<T>& a, cudaStream_t st) {
     const Grid& g = a.g;
-    const long long ne = (long long)g.n * g.n * g.n;
-    const long long nn = (long long)(g.n + 1) * (g.n + 1) * (g.n + 1);
     if (ep3d_scratch_count(g) > a.face_cap) {
         set_error("element scratch too small (%lld < %lld)", a.face_cap, ep3d_scratch_count(g));
         return JFNK_ERR_WORKSPACE;
     }
-    const long long eb = std::min<long long>((ne + kEpElemThreads - 1) / kEpElemThreads, 1LL << 30);
-    ep3d_elem_kernel<T, P, M, ADJ><<<(unsigned)eb, kEpElemThreads, 0, st>>>(a);
+    if (g.n > 1024) {
+        set_error("element-parallel kernels: n = %d beyond 1024 (32-bit node indices, grid rows)", g.n);
+        return JFNK_ERR_INVALID_ARG;
+    }
+    // x-rows of up to 128 elements per block (a whole number of warps)
+    const int bx = std::min(kEpElemThreads, ((g.n + 31) / 32) * 32);
+    ep3d_elem_kernel<T, P, M, ADJ><<<dim3((g.n + bx - 1) / bx, g.n, g.n), bx, 0, st>>>(a);
     JFNK_LAUNCH_CHECK();
-    // the reduction scratch holds 2 kMaxRedBlocks partials: grid-stride beyond
-    const long long nb = std::min<long long>((nn + kEpNodeThreads - 1) / kEpNodeThreads, 2LL * kMaxRedBlocks);
-    ep3d_node_kernel<T, M, ADJ><<<(unsigned)nb, kEpNodeThreads, 0, st>>>(a);
+    // the reduction scratch holds 2 kMaxRedBlocks partials: node rows grid-strided beyond
+    const long long rows = (long long)(g.n + 1) * (g.n + 1);
+    const int nb = (int)std::min<long long>(rows, 2LL * kMaxRedBlocks);
+    ep3d_node_kernel<T, M, ADJ><<<nb, kEpNodeThreads, 0, st>>>(a);
     JFNK_LAUNCH_CHECK();
     return JFNK_OK;
 }

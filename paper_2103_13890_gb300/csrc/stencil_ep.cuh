@@ -13,7 +13,8 @@ inline long long ep3d_scratch_count(const Grid& g) {
 // True when the element-parallel kernels run for these arguments.
 template <typename T>
 inline bool ep3d_use(const StencilArgs<T>& a) {
-    return a.face != nullptr && a.g.d == 3 && a.g.n <= a.ep_max_n && ep3d_scratch_count(a.g) <= a.face_cap;
+    return a.face != nullptr && a.g.d == 3 && !a.g.beam && a.g.n <= a.ep_max_n &&
+           ep3d_scratch_count(a.g) <= a.face_cap;
 }
 
 // adj: the vector-Jacobian product (J^T v, and (dF/dkappa)^T v into a.dkout)

@@ -59,7 +59,7 @@ __device__ __forceinline__ ChebK2<float> cheb_of2<float>(const ChebTable* t, int
 
 // Per-node epilogue (same definitions as the tiled kernel's): val = A(w)_i.
 template <typename T, Mode M>
-__device__ __forceinline__ void epilogue2(const StencilArgs<T>& a, long long idx, bool inner, T val, T inv_eps,
+__device__ __forceinline__ void epilogue2(const StencilArgs<T>& a, int idx, bool inner, T val, T inv_eps,
                                           const ChebK2<T>& ck, float& red) {
     if (M == Mode::F) {
         T f = T(0), av = T(0);
@@ -128,7 +128,7 @@ struct EpiIn {
 };
 
 template <typename T, Mode M>
-__device__ __forceinline__ void epi_load(const StencilArgs<T>& a, long long idx, EpiIn<T>& e) {
+__device__ __forceinline__ void epi_load(const StencilArgs<T>& a, int idx, EpiIn<T>& e) {
     if (M == Mode::F || M == Mode::JV) e.ld = a.load ? a.load[idx] : T(0);
     if (M != Mode::F) e.au = a.Au[idx];
     if (M == Mode::BMJ || M == Mode::CHEB0) e.rhs = a.rhs[idx];
@@ -141,7 +141,7 @@ __device__ __forceinline__ void epi_load(const StencilArgs<T>& a, long long idx,
 
 // Same definitions as epilogue2 for an interior node, operands from e.
 template <typename T, Mode M>
-__device__ __forceinline__ void epilogue2_pf(const StencilArgs<T>& a, long long idx, T val, T inv_eps,
+__device__ __forceinline__ void epilogue2_pf(const StencilArgs<T>& a, int idx, T val, T inv_eps,
                                              const ChebK2<T>& ck, const EpiIn<T>& e, float& red) {
     if (M == Mode::F) {
         const T f = val - (T)a.load_const - e.ld;
@@ -181,17 +181,17 @@ __device__ __forceinline__ void epilogue2_pf(const StencilArgs<T>& a, long long 
 }
 
 // Face buffer addressing
-__device__ __forceinline__ long long ylo_idx(const V2Geom& q, int ty, int c, int zl, int x) {
-    return q.ylo + (((long long)ty * q.Tz + c) * (q.ZC + 1) + zl) * (q.n + 1) + x;
+__device__ __forceinline__ int ylo_idx(const V2Geom& q, int ty, int c, int zl, int x) {
+    return (int)q.ylo + (((int)ty * q.Tz + c) * (q.ZC + 1) + zl) * (q.n + 1) + x;
 }
-__device__ __forceinline__ long long yhi_idx(const V2Geom& q, int ty, int c, int zl, int x) {
-    return q.yhi + (((long long)ty * q.Tz + c) * (q.ZC + 1) + zl) * (q.n + 1) + x;
+__device__ __forceinline__ int yhi_idx(const V2Geom& q, int ty, int c, int zl, int x) {
+    return (int)q.yhi + (((int)ty * q.Tz + c) * (q.ZC + 1) + zl) * (q.n + 1) + x;
 }
-__device__ __forceinline__ long long zlo_idx(const V2Geom& q, int ty, int c, int w, int x) {
-    return q.zlo + (((long long)ty * q.Tz + c) * (q.BY + 1) + w) * (q.n + 1) + x;
+__device__ __forceinline__ int zlo_idx(const V2Geom& q, int ty, int c, int w, int x) {
+    return (int)q.zlo + (((int)ty * q.Tz + c) * (q.BY + 1) + w) * (q.n + 1) + x;
 }
-__device__ __forceinline__ long long zhi_idx(const V2Geom& q, int ty, int c, int w, int x) {
-    return q.zhi + (((long long)ty * q.Tz + c) * (q.BY + 1) + w) * (q.n + 1) + x;
+__device__ __forceinline__ int zhi_idx(const V2Geom& q, int ty, int c, int w, int x) {
+    return (int)q.zhi + (((int)ty * q.Tz + c) * (q.BY + 1) + w) * (q.n + 1) + x;
 }
 
 template <typename T, Prob P, Mode M>
@@ -202,6 +202,7 @@ __global__ void __launch_bounds__(kV2Threads, 1) stencil3d_v2_kernel(const Stenc
     T* C2 = W + 3 * (BY + 1) * NP;          // [2][8][BY][n] (double-buffered by layer parity)
     __shared__ double red_sm[32];
     const Grid g = a.g;
+    const int sy32 = (int)g.sy, sz32 = (int)g.sz;  // (n+1)^3 < 2^31 for n <= 512
     const int tx = threadIdx.x, w = threadIdx.y;
     const int ty = blockIdx.x, c = blockIdx.y;
     const int y0 = ty * BY;
@@ -217,7 +218,7 @@ __global__ void __launch_bounds__(kV2Threads, 1) stencil3d_v2_kernel(const Stenc
 
     // nodal value of w = x + eps v at (x, y, z); boundary entries of v ignored
     auto node_val = [&](int x, int y, int z) -> T {
-        const long long idx = (long long)z * g.sz + (long long)y * g.sy + x;
+        const int idx = (int)z * sz32 + (int)y * sy32 + x;
         T val = a.u[idx];
         if (M != Mode::F) {
             const bool bnd = x == 0 || x == n || y == 0 || y == n || z == 0 || z == n;
@@ -266,7 +267,7 @@ __global__ void __launch_bounds__(kV2Threads, 1) stencil3d_v2_kernel(const Stenc
         const bool pf = (k + 2 <= z1);
         if (pf) load4(k + 2, q0, q1, q2, q3);
         // operands of the node epilogue of this layer (complete nodes only)
-        const long long idxA = (long long)k * g.sz + (long long)yA * g.sy + tx;
+        const int idxA = (int)k * sz32 + (int)yA * sy32 + tx;
         const bool completeA = !(k == 0 || bndA || tx == 0 || faceA || k == z0);
         EpiIn<T> eA;
         if (completeA) epi_load<T, M>(a, idxA, eA);
@@ -277,7 +278,7 @@ __global__ void __launch_bounds__(kV2Threads, 1) stencil3d_v2_kernel(const Stenc
                    W1[(w + 1) * NP + tx],     W1[(w + 1) * NP + tx + 1]};
         T r[8];
         if (P == Prob::NDK3)
-            elem_nd3<T, true>(ue, a.kappa[((long long)k * n + (y0 + w)) * n + tx], r);
+            elem_nd3<T, true>(ue, a.kappa[((int)k * n + (y0 + w)) * n + tx], r);
         else
             elem_nd3<T, false>(ue, T(1), r);
 #pragma unroll
@@ -313,7 +314,7 @@ __global__ void __launch_bounds__(kV2Threads, 1) stencil3d_v2_kernel(const Stenc
         // plane k
         {
             const T vA = loA + carryA;
-            const long long idx = (long long)k * g.sz + (long long)yA * g.sy + tx;
+            const int idx = (int)k * sz32 + (int)yA * sy32 + tx;
             if (k == 0 || bndA || tx == 0) {
                 epilogue2<T, M>(a, idx, false, zero, inv_eps, ck0, red);
             } else if (faceA) {
@@ -328,7 +329,7 @@ __global__ void __launch_bounds__(kV2Threads, 1) stencil3d_v2_kernel(const Stenc
         }
         if (extra_row) {
             const T vB = loB + carryB;
-            const long long idx = (long long)k * g.sz + (long long)yB * g.sy + tx;
+            const int idx = (int)k * sz32 + (int)yB * sy32 + tx;
             if (k == 0 || bndB || tx == 0) {
                 epilogue2<T, M>(a, idx, false, zero, inv_eps, ck0, red);
             } else {
@@ -340,7 +341,7 @@ __global__ void __launch_bounds__(kV2Threads, 1) stencil3d_v2_kernel(const Stenc
     }
     // plane z1: the carries are partial sums from the last layer only
     {
-        const long long idx = (long long)z1 * g.sz + (long long)yA * g.sy + tx;
+        const int idx = (int)z1 * sz32 + (int)yA * sy32 + tx;
         if (z1 == n || bndA || tx == 0) {
             epilogue2<T, M>(a, idx, false, zero, inv_eps, ck0, red);
         } else if (faceA) {
@@ -350,7 +351,7 @@ __global__ void __launch_bounds__(kV2Threads, 1) stencil3d_v2_kernel(const Stenc
         }
         if (extra_col) epilogue2<T, M>(a, idx + 1, false, zero, inv_eps, ck0, red);
         if (extra_row) {
-            const long long idxB = (long long)z1 * g.sz + (long long)yB * g.sy + tx;
+            const int idxB = (int)z1 * sz32 + (int)yB * sy32 + tx;
             if (z1 == n || bndB || tx == 0) {
                 epilogue2<T, M>(a, idxB, false, zero, inv_eps, ck0, red);
             } else {
@@ -370,23 +371,24 @@ template <typename T, Mode M>
 __global__ void __launch_bounds__(256) stencil3d_fixup_kernel(const StencilArgs<T> a, const V2Geom q, int main_blocks) {
     __shared__ double red_sm[32];
     const Grid g = a.g;
+    const int sy32 = (int)g.sy, sz32 = (int)g.sz;
     const int n = q.n, BY = q.BY, ZC = q.ZC;
-    const long long m1 = n - 1;
-    const long long countA = (long long)(q.Ty - 1) * m1 * m1;
-    const long long rowsB = m1 - (q.Ty - 1);
-    const long long countB = (long long)(q.Tz - 1) * rowsB * m1;
+    const int m1 = n - 1;
+    const int countA = (int)(q.Ty - 1) * m1 * m1;
+    const int rowsB = m1 - (q.Ty - 1);
+    const int countB = (int)(q.Tz - 1) * rowsB * m1;
     T inv_eps = T(0);
     if (M != Mode::F) inv_eps = inv_eps_of2<T>(a.eps);
     ChebK2<T> ck = {T(0), T(0), T(0)};
     if (M == Mode::CHEB0 || M == Mode::CHEB || M == Mode::CHEBLAST) ck = cheb_of2<T>(a.cheb, a.cheb_step);
     float red = 0.f;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < countA + countB;
-         i += (long long)gridDim.x * blockDim.x) {
+    for (int i = blockIdx.x * (int)blockDim.x + threadIdx.x; i < countA + countB;
+         i += (int)gridDim.x * blockDim.x) {
         int x, y, z;
         T total;
         if (i < countA) {
             const int tyb = (int)(i / (m1 * m1)) + 1;
-            const long long rem = i % (m1 * m1);
+            const int rem = i % (m1 * m1);
             z = (int)(rem / m1) + 1;
             x = (int)(rem % m1) + 1;
             y = tyb * BY;
@@ -398,9 +400,9 @@ __global__ void __launch_bounds__(256) stencil3d_fixup_kernel(const StencilArgs<
                         (a.face[yhi_idx(q, tyb - 1, cz, 0, x)] + a.face[ylo_idx(q, tyb, cz, 0, x)]);
             }
         } else {
-            const long long j = i - countA;
+            const int j = i - countA;
             const int cb = (int)(j / (rowsB * m1)) + 1;
-            const long long rem = j % (rowsB * m1);
+            const int rem = j % (rowsB * m1);
             const int yi = (int)(rem / m1);
             x = (int)(rem % m1) + 1;
             y = (yi / (BY - 1)) * BY + (yi % (BY - 1)) + 1;
@@ -408,7 +410,7 @@ __global__ void __launch_bounds__(256) stencil3d_fixup_kernel(const StencilArgs<
             const int tyy = y / BY, ww = y - tyy * BY;
             total = a.face[zhi_idx(q, tyy, cb - 1, ww, x)] + a.face[zlo_idx(q, tyy, cb, ww, x)];
         }
-        const long long idx = (long long)z * g.sz + (long long)y * g.sy + x;
+        const int idx = (int)z * sz32 + (int)y * sy32 + x;
         epilogue2<T, M>(a, idx, true, total * a.node_scale, inv_eps, ck, red);
     }
     if (a.red == RedOut::NONE) return;
@@ -432,25 +434,14 @@ __global__ void __launch_bounds__(256) stencil3d_fixup_kernel(const StencilArgs<
         *a.counter = 0u;
         const double nrm = sqrt(s);
         if (a.red_norm) *a.red_norm = nrm;
-        if (a.red == RedOut::EPS) {
-            double e = eps_formula(a.epsp.mode, a.epsp.n_unknowns, *a.epsp.xstat, nrm);
-            double inv = e > 0.0 ? 1.0 / e : 0.0;
-            if (!isfinite(e) || !isfinite(inv)) {
-                if (a.status) atomicOr(a.status, 1);
-                e = 0.0;
-                inv = 0.0;
-            }
-            a.red_eps->e = e;
-            a.red_eps->inv = inv;
-            a.red_eps->ef = (float)e;
-            a.red_eps->invf = (float)inv;
-        }
+        if (a.red == RedOut::EPS || a.red == RedOut::EPS_UNIT)
+            set_eps_slot(a.red_eps, a.epsp, nrm, a.red == RedOut::EPS_UNIT, a.status);
     }
 }
 
 // ---------------------------------------------------------------------------
 bool v2_applicable(const Grid& g) {
-    return g.d == 3 && g.n >= 64 && g.n <= 512 && (g.n % 32) == 0;
+    return g.d == 3 && !g.beam && g.n >= 64 && g.n <= 512 && (g.n % 32) == 0;
 }
 
 V2Geom v2_geometry(const Grid& g, int num_sms) {

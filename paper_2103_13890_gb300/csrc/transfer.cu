@@ -8,6 +8,7 @@
 // fine nodes, so R and P read interior values only; coarse boundary entries
 // are 0 for R and the injected Dirichlet value for P.
 #include "transfer.cuh"
+#include "beam.cuh"
 
 namespace jfnk {
 
@@ -62,6 +63,7 @@ __global__ void restrict_kernel(Grid gc, Grid gf, const T* __restrict__ f, T* __
 
 template <typename T>
 jfnk_status restrict_to(const Grid& gf, const Grid& gc, const T* f, T* c, bool projection, cudaStream_t st) {
+    if (gf.beam) return beam_restrict<T>(gf, gc, f, c, projection, st);
     const T scale = projection ? (gc.d == 3 ? T(0.125) : T(0.25)) : T(1);
     restrict_kernel<T><<<t_blocks(gc.size), kTThreads, 0, st>>>(gc, gf, f, c, scale, projection ? 1 : 0);
     JFNK_LAUNCH_CHECK();
@@ -108,6 +110,7 @@ __global__ void prolong_add_kernel(Grid gf, Grid gc, const T* __restrict__ c, T*
 
 template <typename T>
 jfnk_status prolong_add(const Grid& gc, const Grid& gf, const T* c, T* s, cudaStream_t st) {
+    if (gf.beam) return beam_prolong_add<T>(gc, gf, c, s, st);
     prolong_add_kernel<T><<<t_blocks(gf.size), kTThreads, 0, st>>>(gf, gc, c, s);
     JFNK_LAUNCH_CHECK();
     return JFNK_OK;

@@ -13,15 +13,7 @@ static int vec_blocks(long long len) {
     return (int)(b < kVecBlocks ? (b < 1 ? 1 : b) : kVecBlocks);
 }
 
-__device__ __forceinline__ bool grid_inner(const Grid& g, long long i) {
-    const long long x = i % g.sy;
-    const long long yz = i / g.sy;
-    const long long y = yz % g.ny;
-    const long long z = yz / g.ny;
-    bool in = x > 0 && x < g.nx - 1 && y > 0 && y < g.ny - 1;
-    if (g.d == 3) in = in && z > 0 && z < g.nz - 1;
-    return in;
-}
+__device__ __forceinline__ bool grid_inner(const Grid& g, long long i) { return grid_unknown(g, i); }
 
 // ---------------------------------------------------------------------------
 template <typename T>
@@ -41,14 +33,7 @@ __global__ void masked_stat_kernel(Grid g, const T* x, int what, double* out, do
         double r = (what == 0) ? tot : sqrt(tot);
         if (out) *out = r;
         if (norm_out) *norm_out = r;
-        if (slot) {
-            double e = eps_formula(ep.mode, ep.n_unknowns, *ep.xstat, r);
-            double inv = e > 0.0 ? 1.0 / e : 0.0;
-            slot->e = e;
-            slot->inv = inv;
-            slot->ef = (float)e;
-            slot->invf = (float)inv;
-        }
+        if (slot) set_eps_slot(slot, ep, r, ep.unit != 0, nullptr);
     }
 }
 

@@ -5,6 +5,8 @@ FD-driven components (power method, smoother, coarse GMRES, V-cycle) carry the
 FD round-off of each action (about eps_p / eps relative, ~1e-8 for FP64), so
 GPU and oracle agree to ~1e-6 relative, not to the last bit; transfers are
 exact linear maps and agree to round-off."""
+import functools
+
 import numpy as np
 import pytest
 
@@ -62,22 +64,33 @@ def test_transfers_parity(d, n, dt):
     assert rel(host(out), s0 + transfer.prolong(c)) <= tol
 
 
+@functools.lru_cache(maxsize=None)
+def _oracle_setup(kind, n, levels, pc, seed, lam, nu_pre, nu_post, cheb_degree, power_iters):
+    """The oracle hierarchy after set-up at the seeded state (shared by the tests
+    and kernel paths that use the same case; tests only read it, or set the
+    fields they use before using them)."""
+    d = fem.dim_of(kind)
+    u = random_state_field(n, d, seed=9, kind="mms" if kind == "nd3d" else "uniform",
+                           amplitude=0.1 if kind == "nd3d" else 0.5)
+    load = fem.mms_load(n) if kind == "nd3d" else None
+    lv = jfnk.build_hierarchy(kind, n, levels, lam=lam, load=load)
+    oo = jfnk.Options(nu_pre=nu_pre, nu_post=nu_post, cheb_degree=cheb_degree, power_iters=power_iters,
+                      eps_mode_pc="fp32" if pc == "f32" else "paper", seed=seed)
+    jfnk.setup_levels(lv, u, oo, 0)
+    return lv, oo, u, tuple(x.lam_max for x in lv)
+
+
 def _setup_pair(kind, n, levels, pc="f64", seed=0, lam=5.0, **kw):
     """GPU problem after mg_setup at a seeded state, and the oracle hierarchy
     after the same set-up."""
-    d = fem.dim_of(kind)
     o = _opts(pc_dtype=jf().F32 if pc == "f32" else jf().F64,
               eps_mode_pc=jf().EPS_FP32 if pc == "f32" else jf().EPS_PAPER, seed=seed, **kw)
     p = jf().Problem(kind, n, levels, lam=lam, options=o)
-    u = random_state_field(n, d, seed=9, kind="mms" if kind == "nd3d" else "uniform",
-                           amplitude=0.1 if kind == "nd3d" else 0.5)
-    ud = dev(u)
-    p.mg_setup(ud, 0)
-    load = fem.mms_load(n) if kind == "nd3d" else None
-    lv = jfnk.build_hierarchy(kind, n, levels, lam=lam, load=load)
-    oo = jfnk.Options(nu_pre=o.nu_pre, nu_post=o.nu_post, cheb_degree=o.cheb_degree, power_iters=o.power_iters,
-                      eps_mode_pc="fp32" if pc == "f32" else "paper", seed=seed)
-    jfnk.setup_levels(lv, u, oo, 0)
+    lv, oo, u, lam0 = _oracle_setup(kind, n, levels, pc, seed, lam, o.nu_pre, o.nu_post, o.cheb_degree,
+                                    o.power_iters)
+    for x, lm in zip(lv, lam0):  # a test may have set the GPU's estimates
+        x.lam_max = lm
+    p.mg_setup(dev(u), 0)
     return p, o, lv, oo, u
 
 
@@ -96,8 +109,11 @@ def test_setup_projection_operator_and_power_method(kind, n, levels):
         if l >= 1:
             # same SplitMix64 start vector, 10 FD power iterations on both sides
             assert info["lambda_max"] == pytest.approx(lv[l].lam_max, rel=1e-6), l
+            # the eigenvector estimate is a direction: the library keeps the last
+            # action's output J v/||v||, the oracle the normalised vector
             pv = host(p.level_vector(l, "power"))
-            assert rel(pv, lv[l].power_v) <= 1e-5
+            po = lv[l].power_v
+            assert rel(pv / np.linalg.norm(pv), po / np.linalg.norm(po)) <= 1e-5
 
 
 @pytest.mark.parametrize("kind,n,levels,path", [("bratu2d", 64, 4, "default"), ("nd3d", 32, 4, "default"),
@@ -187,17 +203,22 @@ def test_solve_bratu_matches_discrete_solution(pc):
     assert st["newton_its"] <= 6
 
 
+@functools.lru_cache(maxsize=None)
+def _nd_direct_solution(n):
+    return adjoint.newton_direct("nd3d", np.zeros((n + 1,) * 3), load=fem.mms_load(n))[0]
+
+
 @pytest.mark.parametrize("pc,path", [("f64", "default"), ("f32", "default"), ("f64", "tiled"), ("f32", "ep")])
 def test_solve_nd_matches_discrete_solution(pc, path, monkeypatch):
     kernel_path(monkeypatch, path)
-    n = 32
+    n = 24  # 25^3 nodes, 4 levels down to 3^3 elements (a sparse direct solve at this size is quick)
     o = _opts(rtol_newton=1e-11, nu_pre=2, nu_post=2, cheb_degree=4,
               pc_dtype=jf().F32 if pc == "f32" else jf().F64,
               eps_mode_pc=jf().EPS_FP32 if pc == "f32" else jf().EPS_PAPER)
     p = jf().Problem("nd3d", n, 4, options=o)
     u = torch.zeros((n + 1,) * 3, dtype=torch.float64, device="cuda")
     st = p.solve(u)
-    ud, _ = adjoint.newton_direct("nd3d", np.zeros((n + 1,) * 3), load=fem.mms_load(n))
+    ud = _nd_direct_solution(n)
     assert st["converged"]
     assert rel(host(u), ud) <= 1e-8
 

@@ -5,6 +5,8 @@ Tolerances: F <= 1e-12 relative (FP64) and <= 1e-5 (FP32) at seeded random
 states.  The FD action amplifies rounding of F(u + eps v) by 1/eps: two
 correct FP64 implementations differ by about c eps_p ||F-terms|| / (eps ||Jv||);
 the test computes that bound from the data (c = 64) rather than fixing it."""
+import functools
+
 import numpy as np
 import pytest
 
@@ -46,15 +48,21 @@ PATH_CASES = [(k, n, path) for k, n in CASES for path in ("default", "ep", "tile
               if k != "bratu2d" or path == "default"]
 
 
+@functools.lru_cache(maxsize=None)
+def _oracle_residual_case(kind, n, dirichlet):
+    """(u, kappa, oracle F) of one parity case, shared by the kernel paths."""
+    kap = _kappa(n) if kind == "ndk3d" else None
+    u = _state(kind, n, seed=n, dirichlet=dirichlet)
+    load = fem.mms_load(n) if kind == "nd3d" else None
+    return u, kap, fem.residual(kind, u, 5.0, kap, load)
+
+
 @pytest.mark.parametrize("kind,n,path", PATH_CASES)
 @pytest.mark.parametrize("dirichlet", [0.0, 0.3])
 def test_residual_fp64_fp32_parity(kind, n, path, dirichlet, monkeypatch):
     kernel_path(monkeypatch, path)
-    kap = _kappa(n) if kind == "ndk3d" else None
+    u, kap, F_ora = _oracle_residual_case(kind, n, dirichlet)
     p = _problem(kind, n, kappa=kap)
-    u = _state(kind, n, seed=n, dirichlet=dirichlet)
-    load = fem.mms_load(n) if kind == "nd3d" else None
-    F_ora = fem.residual(kind, u, 5.0, kap, load)
     F64 = host(p.residual(dev(u)))
     assert rel(F64, F_ora) <= 1e-12
     assert np.all(F64[fem.boundary_mask(u.shape)] == 0)
@@ -94,29 +102,37 @@ def _fd_bound(kind, u, v, kap, load, eps):
     return 64 * EPS64 * np.linalg.norm(A_abs) * 2 ** d / eps
 
 
+@functools.lru_cache(maxsize=None)
+def _oracle_jvp_case(kind, n):
+    """Inputs, oracle FD action, its round-off bound and the analytic J v of one
+    case, shared by the kernel paths."""
+    kap = _kappa(n) if kind == "ndk3d" else None
+    load = fem.mms_load(n) if kind == "nd3d" else None
+    u = _state(kind, n, seed=11)
+    v = random_direction(n, fem.dim_of(kind), seed=12)
+    lv = jfnk.Level(kind, n, 5.0, kap, load)
+    Fo = lv.F(u)
+    eps = jfnk.fd_eps(u, v, lv.mask, "paper")
+    Jo = jfnk.fd_jv(lv, u, Fo, v, "paper")
+    bound = _fd_bound(kind, u, v, kap, load, eps) / np.linalg.norm(Jo)
+    Jex = (fem.assemble_jacobian(kind, u, 5.0, kap) @ v.ravel()).reshape(u.shape)
+    return u, v, kap, Jo, bound, Jex
+
+
 @pytest.mark.parametrize("kind,n,path", [("bratu2d", 64, "default"), ("bratu2d", 95, "default"),
                                          ("nd3d", 33, "default"), ("nd3d", 33, "tiled"),
                                          ("ndk3d", 20, "default"), ("ndk3d", 20, "tiled"),
                                          ("nd3d", 64, "default"), ("nd3d", 64, "tiled")])
 def test_jvp_fp64_parity(kind, n, path, monkeypatch):
     kernel_path(monkeypatch, path)
-    kap = _kappa(n) if kind == "ndk3d" else None
-    load = fem.mms_load(n) if kind == "nd3d" else None
+    u, v, kap, Jo, bound, Jex = _oracle_jvp_case(kind, n)
     p = _problem(kind, n, kappa=kap)
-    u = _state(kind, n, seed=11)
-    v = random_direction(n, fem.dim_of(kind), seed=12)
     ud, vd = dev(u), dev(v)
     Fu = p.residual(ud)
     Jv = host(p.jvp(ud, Fu, vd))
-    lv = jfnk.Level(kind, n, 5.0, kap, load)
-    Fo = lv.F(u)
-    eps = jfnk.fd_eps(u, v, lv.mask, "paper")
-    Jo = jfnk.fd_jv(lv, u, Fo, v, "paper")
-    bound = _fd_bound(kind, u, v, kap, load, eps) / np.linalg.norm(Jo)
     err = rel(Jv, Jo)
     assert err <= max(bound, 1e-12), (err, bound)
     # and both approximate the analytic action to FD accuracy
-    Jex = (fem.assemble_jacobian(kind, u, 5.0, kap) @ v.ravel()).reshape(u.shape)
     assert rel(Jv, Jex) <= 1e-5
 
 
