@@ -62,6 +62,10 @@ def load_peaks():
 # as two flops).
 GB300_SMS = 152
 FP64_INST_PER_CLK_SM = 2
+# DRAM bytes (read + write, cold cache) of one fused FP64 Chebyshev step at
+# 129^3 nodes, element + node phase, from the ncu capture summarised in
+# profiles/ep3d_fp64_cheb_n128_full.md (same kernels as timed here)
+EP_CHEB_N128_TRAFFIC = (33.851136 + 72.991488 + 198.790400 + 29.675520) * 1e6
 
 
 def fp64_peak(peaks):
@@ -448,8 +452,10 @@ def main():
         achieved = ops / avg_s / 1e12
         peak = fp64_peak(peaks) / 1e12
         total_ms_all = sum(v[1] for v in prof.values())
+        traffic = EP_CHEB_N128_TRAFFIC if name == "stencil_nd3d_f64_CHEB_n128" else None
         roof = {"kernel": name, "bound": "alu", "achieved": achieved, "peak": peak,
-                "unit": "Top/s (fp64 pipe)", "frac": achieved / peak, "traffic": None,
+                "unit": "Top/s (fp64 pipe)", "frac": achieved / peak, "traffic": traffic,
+                "traffic_unit": "bytes per fused step (element + node phase)",
                 "avg_launch_ms": avg_s * 1e3, "launches": cnt,
                 "share_of_stencil_time": tot / total_ms_all if total_ms_all else None,
                 "timed_region": f"{args.steps} event-bracketed solves after the value's timed region "

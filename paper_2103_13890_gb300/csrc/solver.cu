@@ -113,6 +113,9 @@ struct jfnk_problem {
     // 3D levels with n <= ep_max_n run the element-parallel kernels (per precision)
     int ep_max_n64 = 1 << 20;
     int ep_max_n32 = 64;
+    // CTA-size cap of the halo-free 3D kernel (per precision)
+    int v2_threads64 = 1024;
+    int v2_threads32 = 1024;
     // captured V-cycle (Lf.b -> Lf.s) and the options it was captured for
     cudaGraphExec_t vgraph = nullptr;
     cudaStream_t cap_stream = nullptr;
@@ -178,10 +181,13 @@ static size_t plan(P& p, char* base, const jfnk_options* o) {
     const size_t N = (size_t)gf.size;
     if (const char* e = getenv("JFNK_EP3D_MAX_N_F64")) p.ep_max_n64 = atoi(e);
     if (const char* e = getenv("JFNK_EP3D_MAX_N_F32")) p.ep_max_n32 = atoi(e);
+    if (const char* e = getenv("JFNK_V2_THREADS_F64")) p.v2_threads64 = atoi(e);
+    if (const char* e = getenv("JFNK_V2_THREADS_F32")) p.v2_threads32 = atoi(e);
     long long face = 0;
     for (int l = 0; l <= p.L; ++l) {
         const Grid& g = p.lv[l].g;
-        face = std::max(face, v2_face_count(g));
+        face = std::max(face, v2_face_count(g, p.v2_threads64));
+        face = std::max(face, v2_face_count(g, p.v2_threads32));
         face = std::max(face, beam_scratch_count(g));
         if (g.n <= std::max(p.ep_max_n64, p.ep_max_n32)) face = std::max(face, ep3d_scratch_count(g));
     }
@@ -297,6 +303,7 @@ static StencilArgs<T> base_args(P& p, int l) {
     a.face = reinterpret_cast<T*>(p.face);
     a.face_cap = (long long)(p.face_bytes / sizeof(T));
     a.ep_max_n = sizeof(T) == 8 ? p.ep_max_n64 : p.ep_max_n32;
+    a.v2_threads = sizeof(T) == 8 ? p.v2_threads64 : p.v2_threads32;
     return a;
 }
 

@@ -82,6 +82,7 @@ struct StencilArgs {
     T* face;
     long long face_cap;
     int ep_max_n;
+    int v2_threads;      // cap on the CTA size of the halo-free kernel (0: 1024)
     // adjoint kernel: per-element (dF/dkappa_e)^T v times dk_scale (nullable)
     T* dkout;
     T dk_scale;

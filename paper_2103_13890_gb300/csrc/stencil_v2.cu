@@ -444,15 +444,17 @@ bool v2_applicable(const Grid& g) {
     return g.d == 3 && !g.beam && g.n >= 64 && g.n <= 512 && (g.n % 32) == 0;
 }
 
-V2Geom v2_geometry(const Grid& g, int num_sms) {
+V2Geom v2_geometry(const Grid& g, int num_sms, int max_threads) {
     V2Geom q;
     q.n = g.n;
-    // rows per CTA: the largest divisor of n with n * BY <= kV2Threads, so that
+    if (max_threads <= 0 || max_threads > kV2Threads) max_threads = kV2Threads;
+    // rows per CTA: the largest divisor of n with n * BY <= max_threads, so that
     // the y tiles cover all n element rows exactly
-    q.BY = kV2Threads / g.n;
+    q.BY = std::max(1, max_threads / g.n);
     while (q.BY > 1 && g.n % q.BY != 0) --q.BY;
     q.Ty = g.n / q.BY;
-    // z chunks: minimise waves x layers per CTA over whole waves of one CTA per SM
+    // z chunks: minimise waves x layers per CTA over whole waves of the CTAs an SM holds
+    num_sms *= std::max(1, kV2Threads / (g.n * q.BY));
     int best_tz = 1;
     long long best_cost = -1;
     for (int tz = 1; tz <= g.n; ++tz) {
@@ -477,9 +479,9 @@ V2Geom v2_geometry(const Grid& g, int num_sms) {
     return q;
 }
 
-long long v2_face_count(const Grid& g) {
+long long v2_face_count(const Grid& g, int max_threads) {
     if (!v2_applicable(g)) return 0;
-    return v2_geometry(g, kNumSMs).face_count;
+    return v2_geometry(g, kNumSMs, max_threads).face_count;
 }
 
 static int fixup_blocks(const V2Geom& q) {
@@ -492,7 +494,7 @@ static int fixup_blocks(const V2Geom& q) {
 
 template <typename T, Prob P, Mode M>
 static jfnk_status launch_v2_pm(const StencilArgs<T>& a, cudaStream_t st) {
-    const V2Geom q = v2_geometry(a.g, kNumSMs);
+    const V2Geom q = v2_geometry(a.g, kNumSMs, a.v2_threads);
     if (q.face_count > a.face_cap) {
         set_error("face scratch too small (%lld < %lld)", a.face_cap, q.face_count);
         return JFNK_ERR_WORKSPACE;

@@ -4,12 +4,12 @@
 
 namespace jfnk {
 
-constexpr int kV2Threads = 1024;  // n x BY threads per CTA
+constexpr int kV2Threads = 1024;  // at most n x BY threads per CTA
 
 // Tiling of the halo-free 3D kernel and the layout of its face buffer.
 struct V2Geom {
     int n;    // elements per direction (multiple of 32)
-    int BY;   // element rows per CTA (kV2Threads / n)
+    int BY;   // element rows per CTA (the largest divisor of n with n BY <= the thread cap)
     int Ty;   // y tiles (n / BY)
     int Tz;   // z chunks
     int ZC;   // layers per chunk (last one may be shorter)
@@ -18,8 +18,10 @@ struct V2Geom {
 };
 
 bool v2_applicable(const Grid& g);
-V2Geom v2_geometry(const Grid& g, int num_sms);
-long long v2_face_count(const Grid& g);  // 0 if the v2 kernel does not apply
+// max_threads: cap on n x BY (<= kV2Threads); CTAs of that size share an SM
+// kV2Threads / (n BY) at a time, which the z-chunk choice accounts for
+V2Geom v2_geometry(const Grid& g, int num_sms, int max_threads = kV2Threads);
+long long v2_face_count(const Grid& g, int max_threads = kV2Threads);  // 0 if the v2 kernel does not apply
 
 template <typename T>
 jfnk_status launch_stencil_v2(Prob prob, Mode mode, const StencilArgs<T>& a, cudaStream_t st);
