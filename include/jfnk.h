@@ -51,7 +51,7 @@ typedef enum {
 
 typedef enum { JFNK_F32 = 0, JFNK_F64 = 1 } jfnk_dtype;
 
-/* Problems (Sec. 3 and the configured workloads), Q1 elements, 2^d Gauss points:
+/* Problems (Sec. 3, and nonlinear diffusion), Q1 elements, 2^d Gauss points:
  *  JFNK_BRATU2D  F_i = int grad u.grad phi_i - lambda exp(u) phi_i   (Sec. 3, Bratu)
  *  JFNK_ND3D     F_i = int (1+u^2) grad u.grad phi_i - int f phi_i, f manufactured
  *                from u* = sin(pi x) sin(pi y) sin(pi z)
@@ -109,7 +109,7 @@ typedef struct {
     uint64_t seed;           /* power-method start vector (SplitMix64 stream) */
     int use_graph;           /* 1: capture the V-cycle once in a CUDA graph and replay it */
     /* The paper's own solver variant (Sec. 2 "The coarse level solver", Alg. 1, Sec. 3) */
-    int outer;               /* JFNK_OUTER_FGMRES (configured workloads) or JFNK_OUTER_CG (Sec. 3) */
+    int outer;               /* JFNK_OUTER_FGMRES (default) or JFNK_OUTER_CG (Sec. 3) */
     int coarse_method;       /* JFNK_COARSE_GMRES or JFNK_COARSE_CGQN: CG preconditioned by L-BFGS,
                                 stopped on negative curvature, re-run with the spectral shift (Alg. 1) */
     int lbfgs_pairs;         /* secant pairs kept for the L-BFGS preconditioner (Sec. 3: 20; <= 32) */

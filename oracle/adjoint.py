@@ -5,7 +5,7 @@ TEST INFRASTRUCTURE ONLY -- see ``oracle/__init__.py``.
 newton_direct: Newton's method x <- x - J(x)^-1 F(x) with the assembled analytic
     Jacobian and a sparse direct solve at every step (Sec. 1 with the linear
     system solved exactly).  The discrete solution of F(u) = 0 is unique for the
-    configured problems, so this reaches the same u as the Jacobian-free method
+    problems it is used on here, so this reaches the same u as the Jacobian-free method
     by an independent route; it is the reference for final-solution parity.
 
 adjoint_gradient: for the coefficient problem ndk3d and the loss

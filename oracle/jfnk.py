@@ -15,7 +15,7 @@ Plain FP64 restatement, in the paper's order and notation:
              ||J dx + F|| <= eta ||F||, gradient-evaluation count
              GE = sum_l 2^(-d(L-l)) GE_l.
 
-Readings (the paper is silent or differs from the configured workloads):
+Readings (where the paper is silent, or where the default settings differ from it):
   * n in the eps formula counts interior unknowns; sums run over interior nodes.
   * "fp32" eps mode: eps = sqrt(2^-23) (1 + ||x||_2) / ||u||_2 (used by the
     single-precision preconditioner; evaluated here in FP64).
@@ -27,11 +27,11 @@ Readings (the paper is silent or differs from the configured workloads):
   * Power method: lambda = ||J v|| for ||v|| = 1 after a fixed number of
     iterations, or the paper's stopping rule |lambda_i - lambda_(i-1)| < tol
     read relative to lambda_i.
-  * Coarse solve: unrestarted GMRES (the configured workloads use GMRES where
+  * Coarse solve: unrestarted GMRES (the default settings use GMRES where
     the paper uses CG), x0 = 0, modified Gram-Schmidt, stop at
     ||r|| <= tol ||r_0|| (relative reading) or after n_0 iterations.
-  * Outer Krylov: right-preconditioned flexible GMRES(m) (the configured
-    workloads; the paper uses CG because its J is symmetric).
+  * Outer Krylov: right-preconditioned flexible GMRES(m) (the default
+    settings; the paper uses CG because its J is symmetric, see pcg).
   * Forcing term: eta = min(0.5, ||F_k|| / ||F_0||) (relative reading of
     eta = min(0.5, ||F||)); the paper's absolute form is an option.
   * Line search: backtracking with quadratic then cubic interpolation

@@ -1,6 +1,6 @@
 // Coarse-level solve of Algorithm 1 (l = 0): a matrix-free Krylov method in
-// place of a direct solver (Sec. 2, "The coarse level solver").  The configured
-// workloads use unrestarted GMRES with x0 = 0; it stops when the Givens
+// place of a direct solver (Sec. 2, "The coarse level solver").  The default
+// settings use unrestarted GMRES with x0 = 0; it stops when the Givens
 // residual estimate is <= tol ||r0|| (relative reading) or <= tol (absolute),
 // or after maxit iterations (Sec. 3: maxit = number of coarse unknowns).
 //
@@ -16,6 +16,14 @@
 namespace jfnk {
 
 constexpr int kCoarseThreads = 512;
+
+// Threads of the one-CTA coarse solvers: about one per node, in whole warps,
+// 64 to 512 (block-wide reductions and barriers dominate on the small coarse
+// grids, and they are cheaper with fewer warps).
+static int coarse_threads(const Grid& g) {
+    const long long t = ((g.size + 31) / 32) * 32;
+    return (int)(t < 64 ? 64 : (t > kCoarseThreads ? kCoarseThreads : t));
+}
 
 // element contributions per element: 2^d (scalar) or 24 (beam)
 __host__ __device__ inline int coarse_npe(const Grid& g) { return g.beam ? 24 : (g.d == 3 ? 8 : 4); }
@@ -639,7 +647,7 @@ static jfnk_status launch_coarse_cgqn(Prob prob, const CoarseArgs<T>& a, cudaStr
     do {                                                                                             \
         JFNK_CUDA_TRY(cudaFuncSetAttribute(coarse_cgqn_kernel<T, PP>,                                 \
                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)); \
-        coarse_cgqn_kernel<T, PP><<<1, kCoarseThreads, smem, st>>>(a);                                \
+        coarse_cgqn_kernel<T, PP><<<1, coarse_threads(a.g), smem, st>>>(a);                                \
     } while (0)
     switch (prob) {
         case Prob::BRATU2: JFNK_CGQN_LAUNCH(Prob::BRATU2); break;
@@ -673,7 +681,7 @@ jfnk_status launch_coarse(Prob prob, const CoarseArgs<T>& a, cudaStream_t st) {
     do {                                                                                             \
         JFNK_CUDA_TRY(cudaFuncSetAttribute(coarse_gmres_kernel<T, PP, ADJ>,                           \
                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)); \
-        coarse_gmres_kernel<T, PP, ADJ><<<1, kCoarseThreads, smem, st>>>(a);                          \
+        coarse_gmres_kernel<T, PP, ADJ><<<1, coarse_threads(a.g), smem, st>>>(a);                          \
     } while (0)
     switch (prob) {
         case Prob::BRATU2: JFNK_COARSE_LAUNCH(Prob::BRATU2, false); break;
@@ -711,7 +719,7 @@ jfnk_status launch_coarse_batched(const CoarseArgs<T>& a0, const CoarseArgs<T>* 
     const size_t smem = coarse_smem_bytes<T>(a0.g, a0.maxit);
     JFNK_CUDA_TRY(cudaFuncSetAttribute(coarse_gmres_batched_kernel<T, Prob::BRATU2, false>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    coarse_gmres_batched_kernel<T, Prob::BRATU2, false><<<count, kCoarseThreads, smem, st>>>(dev_args);
+    coarse_gmres_batched_kernel<T, Prob::BRATU2, false><<<count, coarse_threads(a0.g), smem, st>>>(dev_args);
     JFNK_LAUNCH_CHECK();
     return JFNK_OK;
 }

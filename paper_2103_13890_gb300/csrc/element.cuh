@@ -1,7 +1,7 @@
 // Element arithmetic of the Q1 residuals with the 2^d-point Gauss rule.
 //
 // The element integrals are the ones of the problem definitions (Sec. 3 and
-// the configured workloads): for a Q1 element with nodal values u_abc
+// the nonlinear-diffusion problems): for a Q1 element with nodal values u_abc
 //   R_abc = sum_q w_q [ c(u_q) grad u_q . grad phi_abc(q) (+ source term) ]
 // with Gauss points 1/2 +- 1/(2 sqrt 3) per direction.
 //

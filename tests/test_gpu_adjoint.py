@@ -57,13 +57,29 @@ def test_vjp_parity(kind, n, dt, path, monkeypatch):
         assert rel(host(JTw), JaT) <= 1e-12
 
 
-def _adjoint_case(n, levels, pc="f64"):
+@functools.lru_cache(maxsize=None)
+def _observations(n):
+    """kappa, and u_obs from the second coefficient field plus 1 % noise."""
     kap = kappa_field(n, seed=5)
     kap2 = kappa_field(n, seed=6)
+    u_obs, _ = adjoint.newton_direct("ndk3d", np.zeros((n + 1,) * 3), kappa=kap2)
+    return kap, u_obs + noise_like(u_obs, 0.01, seed=7)
+
+
+@functools.lru_cache(maxsize=None)
+def _oracle_adjoint(n):
+    """The oracle's forward solution, adjoint and gradient (exact Newton, sparse
+    direct adjoint solve), shared by the precisions and kernel paths."""
+    kap, u_obs = _observations(n)
+    u_ora, _ = adjoint.newton_direct("ndk3d", np.zeros((n + 1,) * 3), kappa=kap)
+    grad_ora, lam_ora = adjoint.adjoint_gradient(u_ora, kap, u_obs)
+    return u_ora, grad_ora, lam_ora
+
+
+def _adjoint_case(n, levels, pc="f64"):
+    kap, u_obs = _observations(n)
     o = _opts(pc)
     p = jf().Problem("ndk3d", n, levels, kappa=torch.as_tensor(kap), options=o)
-    u_obs, _ = adjoint.newton_direct("ndk3d", np.zeros((n + 1,) * 3), kappa=kap2)
-    u_obs = u_obs + noise_like(u_obs, 0.01, seed=7)
     return p, o, kap, u_obs
 
 
@@ -79,9 +95,8 @@ def test_adjoint_solve_matches_oracle_adjoint(pc, path, monkeypatch):
     assert st["converged"]
     g = u - dev(u_obs)
     lam, gk, ast = p.adjoint_solve(u, g, rtol=1e-12)
-    u_ora, _ = adjoint.newton_direct("ndk3d", np.zeros((n + 1,) * 3), kappa=kap)
+    u_ora, grad_ora, lam_ora = _oracle_adjoint(n)
     assert rel(host(u), u_ora) <= 1e-8
-    grad_ora, lam_ora = adjoint.adjoint_gradient(u_ora, kap, u_obs)
     assert rel(host(lam), lam_ora) <= 1e-8
     assert rel(host(gk), grad_ora) <= 1e-8
     assert ast["linear_its"] <= 60
@@ -90,8 +105,8 @@ def test_adjoint_solve_matches_oracle_adjoint(pc, path, monkeypatch):
 @pytest.mark.parametrize("n,levels,ndir", [(32, 4, 6), (128, 6, 16)])
 def test_gradient_matches_central_differences(n, levels, ndir):
     """Central differences of the loss along seeded directions dkappa = kappa * z,
-    each loss from a GPU forward solve, against grad_kappa . dkappa (the
-    configured check uses 16 directions at 129^3 nodes)."""
+    each loss from a GPU forward solve, against grad_kappa . dkappa (16
+    directions at 129^3 nodes, the size of the coefficient workload)."""
     kap = kappa_field(n, seed=5)
     kap2 = kappa_field(n, seed=6)
     o = _opts("f64", rtol=1e-11)

@@ -43,7 +43,7 @@ def test_batch_matches_single_and_exact_solutions(pc, graph):
 
 
 def test_batch_of_64_uneven_instances():
-    """The configured batch: 64 instances, sizes from {129^2, 257^2, 513^2} nodes,
+    """The 64-instance batch workload: 64 instances, sizes from {129^2, 257^2, 513^2} nodes,
     lambda ~ U[1, 6.5] (seeded), FP32 preconditioner, FP64 outer, 1e-8."""
     inst = batch_instances(64, seed=4)
     o = _opts("f32", rtol=1e-8)

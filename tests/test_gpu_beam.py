@@ -98,7 +98,7 @@ def test_paper_solver_matches_oracle(k):
 
 
 def test_fgmres_solve_with_fp32_preconditioner():
-    """The configured solver (FGMRES, GMRES coarse solve) with an FP32
+    """The default solver (FGMRES, GMRES coarse solve) with an FP32
     preconditioner also reaches the oracle's discrete solution."""
     k, m = 2, 4
     u0 = hyper.boundary_state(m)
@@ -136,3 +136,28 @@ def test_vcycle_parity_with_cgqn_coarse_solve(amp):
         s = host(p.mg_vcycle(dev(b)))
         so = jfnk.mg_vcycle(lvs, k, b, oo)
         assert rel(s, so) <= 1e-5, rel(s, so)
+
+
+def test_vcycle_parity_near_the_solution():
+    """At the oracle's iterate after four Newton steps of the paper's solver at
+    L2 (a twisted state whose coarse Jacobian the shifted CG has to handle),
+    one V-cycle of the GPU agrees with the oracle's: the first cycle builds the
+    L-BFGS pairs, later ones use them."""
+    k, m = 2, 4
+    lvs0 = jfnk.build_hyper_hierarchy(k)
+    u, _ = jfnk.newton_solve(lvs0, hyper.boundary_state(m), jfnk.paper_options(max_newton=4))
+    p = jf().Problem("beam3d", m, k + 1, options=jf().paper_options())
+    p.mg_setup(dev(u), 0)
+    lvs = jfnk.build_hyper_hierarchy(k)
+    oo = jfnk.paper_options()
+    jfnk.setup_levels(lvs, u, oo, 0)
+    for l in range(1, k + 1):
+        lvs[l].lam_max = p.level_info(l)["lambda_max"]
+    rng = np.random.default_rng(10)
+    errs = []
+    for _ in range(3):
+        b = np.where(hyper.unknown_mask(u.shape), rng.normal(size=u.shape), 0.0)
+        s = host(p.mg_vcycle(dev(b)))
+        so = jfnk.mg_vcycle(lvs, k, b, oo)
+        errs.append(rel(s, so))
+    assert max(errs) <= 1e-5, errs

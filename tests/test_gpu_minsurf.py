@@ -1,6 +1,6 @@
 """GPU parity of the minimal-surface problem (Sec. 3, "Minimal Surface") against
 the oracle through the C ABI: the residual element by element, the FD action,
-and whole JFNK-MG solves (configured FGMRES settings and the paper's own
+and whole JFNK-MG solves (the default FGMRES settings and the paper's own
 settings) on the paper's Dirichlet data u = x(1-x) on y = 0, 1 and 0 on
 x = 0, 1."""
 import numpy as np

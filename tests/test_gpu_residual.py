@@ -74,7 +74,7 @@ def test_residual_fp64_fp32_parity(kind, n, path, dirichlet, monkeypatch):
                                          ("nd3d", 128, "tiled"), ("nd3d", 256, "default"),
                                          ("ndk3d", 128, "default")])
 def test_residual_full_size_sampled(kind, n, path, monkeypatch):
-    """At the configured full sizes: the oracle evaluates F at 60 sampled nodes
+    """At the full workload sizes: the oracle evaluates F at 60 sampled nodes
     (its own element routine on the 2^d elements around each)."""
     kernel_path(monkeypatch, path)
     kap = _kappa(n) if kind == "ndk3d" else None

@@ -90,7 +90,7 @@ def test_discrete_solution_converges_to_scherk_surface():
     assert all(1.8 <= r <= 2.3 for r in rates), (errs, rates)
 
 
-@pytest.mark.parametrize("opts", ["configured", "paper"])
+@pytest.mark.parametrize("opts", ["default", "paper"])
 def test_jfnk_mg_solve_matches_exact_newton(opts):
     """The oracle's JFNK-MG solve of the Sec. 3 minimal-surface problem reaches
     the exact-Newton discrete solution."""

@@ -1,4 +1,4 @@
-"""Seeded synthetic inputs shaped like the configured workloads.
+"""Seeded synthetic inputs shaped like the solver's target workloads (listed below).
 
 This module is the only code shared by the oracle side (tests, CPU baseline)
 and the CUDA side (tests, bench).  It holds none of the method's arithmetic:
