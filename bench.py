@@ -211,9 +211,22 @@ def batched_extra(jf, torch):
     run_seq()
     torch.cuda.synchronize()
     t_seq = time.perf_counter() - t0
+    # the plain FP64 solver (FP64 preconditioner), instance by instance
+    o64 = jf.default_options(rtol_newton=1e-8)
+    p64s = [jf.Problem("bratu2d", nn, lv(nn), lam=lam, options=o64) for nn, lam in inst]
+    for p_, x in zip(p64s, bus):
+        x.zero_()
+        p_.solve(x, o64)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for p_, x in zip(p64s, bus):
+        x.zero_()
+        p_.solve(x, o64)
+    torch.cuda.synchronize()
+    t_seq64 = time.perf_counter() - t0
     return {"workload": "64 x bratu2d, n in {129^2, 257^2, 513^2} nodes, lambda~U[1,6.5] seed 4, FP32 PC, rtol 1e-8",
             "nodes": int(sum((nn + 1) ** 2 for nn, _ in inst)), "batched_s": t_batch, "sequential_s": t_seq,
-            "speedup": t_seq / t_batch, "converged": int(sum(s["converged"] for s in bst)),
+            "speedup": t_seq / t_batch, "sequential_fp64_s": t_seq64, "speedup_vs_fp64": t_seq64 / t_batch, "converged": int(sum(s["converged"] for s in bst)),
             "max_newton_its": max(s["newton_its"] for s in bst)}
 
 

@@ -249,7 +249,9 @@ jfnk_status jfnk_level_info(jfnk_problem* p, int level, double* lambda_max, doub
                             void* stream);
 
 /* Copy a level vector set by jfnk_mg_setup into out (opts->pc_dtype):
- * which = 0: x_l, 1: A(x_l), 2: the power-method vector. */
+ * which = 0: x_l, 1: A(x_l), 2: the power-method vector -- the output J v/||v||
+ * of the last power iteration, whose direction is the eigenvector estimate and
+ * whose norm is lambda_l (the adjoint solve keeps it normalised). */
 jfnk_status jfnk_level_vector(jfnk_problem* p, int level, int which, void* out, void* stream);
 
 /* ---- adjoint: vector-Jacobian products and the adjoint solve --------------

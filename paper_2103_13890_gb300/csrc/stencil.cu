@@ -197,7 +197,7 @@ template <typename T>
 static jfnk_status launch_stencil_impl(Prob prob, Mode mode, const StencilArgs<T>& a, cudaStream_t st) {
     if (prob == Prob::BEAM3) return launch_beam<T>(mode, a, st);
     if (!is_2d(prob) && ep3d_use(a)) return launch_ep3d<T>(prob, mode, false, a, st);
-    if (!is_2d(prob) && a.face != nullptr && v2_applicable(a.g))
+    if (!is_2d(prob) && a.face != nullptr && a.v2_threads >= 0 && v2_applicable(a.g))
         return launch_stencil_v2<T>(prob, mode, a, st);
     switch (prob) {
         case Prob::BRATU2: return dispatch_mode<T, Prob::BRATU2>(mode, a, st);

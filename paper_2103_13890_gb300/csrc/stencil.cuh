@@ -82,7 +82,7 @@ struct StencilArgs {
     T* face;
     long long face_cap;
     int ep_max_n;
-    int v2_threads;      // cap on the CTA size of the halo-free kernel (0: 1024)
+    int v2_threads;      // cap on the CTA size of the halo-free kernel (0: 1024; < 0: not used)
     // adjoint kernel: per-element (dF/dkappa_e)^T v times dk_scale (nullable)
     T* dkout;
     T dk_scale;
