@@ -17,7 +17,8 @@ roofline: the dominant kernel (the FP64 element-residual kernel with the fused
          solves right after the timed ones (the value itself is timed without
          per-launch events, V-cycles replayed from their CUDA graph); FP64-ALU
          bound.
-extras:  also the 64-instance batched Bratu solve vs the same instances one by
+extras:  also the same problem on 257^3 nodes, FP32 vs FP64 preconditioner,
+         the 64-instance batched Bratu solve vs the same instances one by
          one, the forward + adjoint solve of the coefficient problem, and the
          paper's own solver variant on Bratu and the minimal surface at its
          refinement levels L1..L5.
@@ -262,6 +263,57 @@ def adjoint_extra(jf, torch, n, shape, stream):
             "adjoint_fgmres_its": ast["linear_its"]}
 
 
+def large_extra(jf, torch, stream, hbm):
+    """Nonlinear diffusion on 257^3 nodes (16.6M unknowns, 7 levels): the
+    FP32-preconditioned solve (FP64 Newton/FGMRES) against the all-FP64 solve
+    on the same GPU, and the residual-evaluation rate at that size."""
+    n, levels = 256, 7
+    shape = (n + 1,) * 3
+    u = torch.zeros(shape, dtype=torch.float64, device="cuda")
+    out = {"workload": "nd3d_257^3 V(2,2) cheb4 fgmres30 rtol1e-8, 7 levels", "unknowns": (n - 1) ** 3}
+    sols = {}
+    for pc, reps in (("f64", 1), ("f32", 2)):
+        o = jf.default_options(nu_pre=2, nu_post=2, cheb_degree=4, rtol_newton=1e-8,
+                               pc_dtype=jf.F32 if pc == "f32" else jf.F64,
+                               eps_mode_pc=jf.EPS_FP32 if pc == "f32" else jf.EPS_PAPER)
+        p = jf.Problem("nd3d", n, levels, options=o)
+        u.zero_()
+        p.solve(u)
+        torch.cuda.synchronize()
+        ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ea.record(stream)
+        for _ in range(reps):
+            u.zero_()
+            st = p.solve(u)
+        eb.record(stream)
+        torch.cuda.synchronize()
+        out[pc + "_pc_s"] = ea.elapsed_time(eb) / reps * 1e-3
+        out[pc + "_pc_its"] = {"newton": st["newton_its"], "fgmres": st["linear_its"], "converged": bool(st["converged"])}
+        sols[pc] = u.clone()
+        if pc == "f64":
+            resid = {}
+            for dt, name in ((torch.float64, "f64"), (torch.float32, "f32")):
+                uu = torch.rand(shape, dtype=dt, device="cuda")
+                FF = torch.empty_like(uu)
+                for _ in range(3):
+                    p.residual(uu, out=FF)
+                ea.record(stream)
+                for _ in range(10):
+                    p.residual(uu, out=FF)
+                eb.record(stream)
+                torch.cuda.synchronize()
+                t = ea.elapsed_time(eb) / 10 * 1e-3
+                byts = 3 * (8 if name == "f64" else 4) * (n + 1) ** 3
+                resid[name] = {"dof_per_s": (n - 1) ** 3 / t, "ms": t * 1e3, "achieved_gbs": byts / t / 1e9,
+                               "pct_hbm": 100.0 * byts / t / 1e9 / hbm}
+                del uu, FF
+            out["residual_eval"] = resid
+        del p
+    out["speedup_fp32_pc"] = out["f64_pc_s"] / out["f32_pc_s"]
+    out["rel_diff_fp32_vs_fp64_solution"] = float((sols["f32"] - sols["f64"]).norm() / sols["f64"].norm())
+    return out
+
+
 def paper_variant_extra(jf, torch, stream):
     """The paper's own solver (outer CG, V(5,5), coarse CG with L-BFGS and the
     spectral shift, ||F|| < 1e-6) on its three examples at the refinement levels
@@ -454,6 +506,7 @@ def main():
     batch = batched_extra(jf, torch)
     adj = adjoint_extra(jf, torch, n, shape, stream)
     paper = paper_variant_extra(jf, torch, stream)
+    large = large_extra(jf, torch, stream, hbm)
 
     # ---- roofline of the dominant kernel ---------------------------------------
     top = max(prof.items(), key=lambda kv: kv[1][1]) if prof else None
@@ -496,6 +549,7 @@ def main():
                         "newton_its": st32["newton_its"], "fgmres_its": st32["linear_its"],
                         "rel_diff_vs_fp64_solution": sol_diff},
             "residual_eval": resid,
+            "fp32_vs_fp64_pc_257": large,
             "batched": batch,
             "adjoint": adj,
             "paper_variant": paper,

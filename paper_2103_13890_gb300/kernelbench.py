@@ -4,7 +4,8 @@
 
 op: residual | jvp | smooth (one Chebyshev application = start + fused steps)
     | vcycle | solve (a whole JFNK-MG solve from u0 = 0 to 1e-8, preconditioner
-    in --dtype).  Prints one JSON line with the mean time per call (CUDA events
+    in --dtype) | batch (the batched solve of 64 uneven 2D Bratu instances,
+    sizes from {129^2, 257^2, 513^2} nodes, lambda ~ U[1, 6.5], seed 4).  Prints one JSON line with the mean time per call (CUDA events
 on the current stream, after warm-up) and, for the element kernels, the
 achieved FP64/FP32 operation rate and HBM bandwidth of the algorithmic traffic.
 
@@ -26,13 +27,15 @@ def main():
     ap.add_argument("--kind", default="nd3d", choices=list(OPS_PER_ELEMENT))
     ap.add_argument("--n", type=int, default=128)
     ap.add_argument("--levels", type=int, default=0, help="0: coarsest level with 4 elements")
-    ap.add_argument("--op", default="residual", choices=["residual", "jvp", "smooth", "vcycle", "solve"])
+    ap.add_argument("--op", default="residual", choices=["residual", "jvp", "smooth", "vcycle", "solve", "batch"])
     ap.add_argument("--dtype", default="f64", choices=["f64", "f32"])
     ap.add_argument("--reps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--rtol", type=float, default=1e-8)
     ap.add_argument("--profiler-range", action="store_true")
     a = ap.parse_args()
+    if a.op == "batch":
+        return batch_main(a)
     d = 2 if a.kind == "bratu2d" else 3
     n = a.n
     levels = a.levels
@@ -108,6 +111,38 @@ def main():
     if words:
         line["gbs"] = words * w * nodes / (ms * 1e-3) / 1e9
     print(json.dumps(line))
+
+
+def batch_main(a):
+    import math
+
+    from workloads import batch_instances
+    inst = batch_instances(64, seed=4)
+    o = jf.default_options(rtol_newton=1e-8, pc_dtype=jf.F64 if a.dtype == "f64" else jf.F32,
+                           eps_mode_pc=jf.EPS_PAPER if a.dtype == "f64" else jf.EPS_FP32)
+    ps = [jf.Problem("bratu2d", nn, int(round(math.log2(nn // 8))) + 1, lam=lam, options=o) for nn, lam in inst]
+    us = [torch.zeros((nn + 1, nn + 1), dtype=torch.float64, device="cuda") for nn, _ in inst]
+
+    def call():
+        for x in us:
+            x.zero_()
+        return jf.solve_batched(ps, us, o)
+
+    for _ in range(a.warmup):
+        call()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if a.profiler_range:
+        torch.cuda.profiler.start()
+    e0.record()
+    for _ in range(a.reps):
+        st = call()
+    e1.record()
+    torch.cuda.synchronize()
+    if a.profiler_range:
+        torch.cuda.profiler.stop()
+    print(json.dumps({"op": "batch", "instances": len(inst), "dtype": a.dtype, "ms": e0.elapsed_time(e1) / a.reps,
+                      "converged": int(sum(s["converged"] for s in st))}))
 
 
 if __name__ == "__main__":
