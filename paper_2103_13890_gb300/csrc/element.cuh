@@ -25,6 +25,13 @@
 
 namespace jfnk {
 
+// a b + c (the compiler contracts it to one FMA for float and double; the
+// packed two-element type of the FP32 kernels overloads it)
+template <typename T>
+__host__ __device__ __forceinline__ T madd(T a, T b, T c) {
+    return a * b + c;
+}
+
 // 2-point butterfly over two sign variables, forward:
 //   out[i][j] = v00 + s_i v10 + s_j v01 + s_i s_j v11,  s_0 = -1, s_1 = +1
 template <typename T>
@@ -69,14 +76,17 @@ __host__ __device__ __forceinline__ void elem_nd3(const T u[8], T kap, T r[8]) {
     T a00 = p0 + p1, a01 = p1 - p0, b00 = p2 + p3, b01 = p3 - p2;  // x-mode 0
     T a10 = q0 + q1, a11 = q1 - q0, b10 = q2 + q3, b11 = q3 - q2;  // x-mode 1
     // S_pqr = M'_pqr A^(p+q+r) / 8  (8 ops)
+    // (A^k / 8 is exact in either precision: the scaling by 2^-3 does not round)
+    const T A1s = T(0.57735026918962576451 * 0.125), A2s = T(0.33333333333333333333 * 0.125),
+            A3s = T(0.19245008972987525484 * 0.125);
     T S000 = (a00 + b00) * T(0.125);
-    T S001 = (b00 - a00) * (A1 * T(0.125));
-    T S010 = (a01 + b01) * (A1 * T(0.125));
-    T S011 = (b01 - a01) * (A2 * T(0.125));
-    T S100 = (a10 + b10) * (A1 * T(0.125));
-    T S101 = (b10 - a10) * (A2 * T(0.125));
-    T S110 = (a11 + b11) * (A2 * T(0.125));
-    T S111 = (b11 - a11) * (A3 * T(0.125));
+    T S001 = (b00 - a00) * A1s;
+    T S010 = (a01 + b01) * A1s;
+    T S011 = (b01 - a01) * A2s;
+    T S100 = (a10 + b10) * A1s;
+    T S101 = (b10 - a10) * A2s;
+    T S110 = (a11 + b11) * A2s;
+    T S111 = (b11 - a11) * A3s;
     // values and (scaled) gradients at the Gauss points (40 ops)
     T P0[2][2], GX[2][2], GY[2][2], GZ[2][2];
     h2_fwd(S000, S010, S001, S011, P0);  // [sy][sz]
@@ -92,11 +102,11 @@ __host__ __device__ __forceinline__ void elem_nd3(const T u[8], T kap, T r[8]) {
             T up = P0[j][k] + GX[j][k];
             T um = P0[j][k] - GX[j][k];
             if (KAPPA) {
-                c[1][j][k] = (kap * up) * up + kap;
-                c[0][j][k] = (kap * um) * um + kap;
+                c[1][j][k] = madd(kap * up, up, kap);
+                c[0][j][k] = madd(kap * um, um, kap);
             } else {
-                c[1][j][k] = up * up + T(1);
-                c[0][j][k] = um * um + T(1);
+                c[1][j][k] = madd(up, up, T(1));
+                c[0][j][k] = madd(um, um, T(1));
             }
         }
     // sum the flux over the direction its gradient factor does not depend on

@@ -116,6 +116,9 @@ struct jfnk_problem {
     // CTA-size cap of the halo-free 3D kernel (per precision)
     int v2_threads64 = 1024;
     int v2_threads32 = 1024;
+    // FP32 levels on the halo-free tiling run its paired-element variant
+    // (0: not used; 1 / 2: one / two CTAs per SM; 3: chosen per mode)
+    int v3_f32 = 3;
     // captured V-cycle (Lf.b -> Lf.s) and the options it was captured for
     cudaGraphExec_t vgraph = nullptr;
     cudaStream_t cap_stream = nullptr;
@@ -183,11 +186,16 @@ static size_t plan(P& p, char* base, const jfnk_options* o) {
     if (const char* e = getenv("JFNK_EP3D_MAX_N_F32")) p.ep_max_n32 = atoi(e);
     if (const char* e = getenv("JFNK_V2_THREADS_F64")) p.v2_threads64 = atoi(e);
     if (const char* e = getenv("JFNK_V2_THREADS_F32")) p.v2_threads32 = atoi(e);
+    if (const char* e = getenv("JFNK_V3_F32")) p.v3_f32 = atoi(e);
     long long face = 0;
     for (int l = 0; l <= p.L; ++l) {
         const Grid& g = p.lv[l].g;
         face = std::max(face, v2_face_count(g, p.v2_threads64));
         face = std::max(face, v2_face_count(g, p.v2_threads32));
+        if (p.v3_f32) {
+            face = std::max(face, v3_face_count(g, p.v2_threads32, 1));
+            face = std::max(face, v3_face_count(g, p.v2_threads32, 2));
+        }
         face = std::max(face, beam_scratch_count(g));
         if (g.n <= std::max(p.ep_max_n64, p.ep_max_n32)) face = std::max(face, ep3d_scratch_count(g));
     }
@@ -304,6 +312,7 @@ static StencilArgs<T> base_args(P& p, int l) {
     a.face_cap = (long long)(p.face_bytes / sizeof(T));
     a.ep_max_n = sizeof(T) == 8 ? p.ep_max_n64 : p.ep_max_n32;
     a.v2_threads = sizeof(T) == 8 ? p.v2_threads64 : p.v2_threads32;
+    a.v3 = sizeof(T) == 4 ? p.v3_f32 : 0;
     return a;
 }
 

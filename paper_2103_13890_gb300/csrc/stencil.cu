@@ -197,8 +197,12 @@ template <typename T>
 static jfnk_status launch_stencil_impl(Prob prob, Mode mode, const StencilArgs<T>& a, cudaStream_t st) {
     if (prob == Prob::BEAM3) return launch_beam<T>(mode, a, st);
     if (!is_2d(prob) && ep3d_use(a)) return launch_ep3d<T>(prob, mode, false, a, st);
-    if (!is_2d(prob) && a.face != nullptr && a.v2_threads >= 0 && v2_applicable(a.g))
+    if (!is_2d(prob) && a.face != nullptr && a.v2_threads >= 0 && v2_applicable(a.g)) {
+        if constexpr (sizeof(T) == 4) {
+            if (a.v3) return launch_stencil_v3(prob, mode, a, st);
+        }
         return launch_stencil_v2<T>(prob, mode, a, st);
+    }
     switch (prob) {
         case Prob::BRATU2: return dispatch_mode<T, Prob::BRATU2>(mode, a, st);
         case Prob::MINSURF2: return dispatch_mode<T, Prob::MINSURF2>(mode, a, st);

@@ -83,6 +83,8 @@ struct StencilArgs {
     long long face_cap;
     int ep_max_n;
     int v2_threads;      // cap on the CTA size of the halo-free kernel (0: 1024; < 0: not used)
+    int v3;              // FP32: the halo-free kernel's two-elements-per-thread variant (0: not used;
+                         // 1 / 2: one / two CTAs per SM; other: chosen per mode)
     // adjoint kernel: per-element (dF/dkappa_e)^T v times dk_scale (nullable)
     T* dkout;
     T dk_scale;

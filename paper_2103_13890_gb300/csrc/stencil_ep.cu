@@ -92,43 +92,42 @@ __global__ void __launch_bounds__(kEpElemThreads) ep3d_elem_kernel(const Stencil
     for (int c = 0; c < 8; ++c) C[c * ne] = r[c];
 }
 
-// Node rows (Y, Z) grid-strided over the blocks (the last-block reduction holds
-// at most 2 kMaxRedBlocks partials), X over the threads of the block.
+// Nodes in storage order, one per thread, grid-strided over the blocks (the
+// last-block reduction holds at most 2 kMaxRedBlocks partials): every thread
+// of every block has a node on all levels, including rows of n+1 nodes that
+// do not fill whole blocks.
 template <typename T, Mode M, bool ADJ>
 __global__ void __launch_bounds__(kEpNodeThreads) ep3d_node_kernel(const StencilArgs<T> a) {
     __shared__ double red_sm[32];
     const Grid g = a.g;
     const int n = g.n, NP = n + 1;
     const long long ne = (long long)n * n * n;
-    const int sy = (int)g.sy, sz = (int)g.sz;
     const int esy = n, esz = n * n;  // element strides
+    const int nodes = NP * NP * NP;  // node index = Z sz + Y sy + X (dense grid)
     const T* C = a.face;
     T inv_eps = T(0);
     if (!ADJ && M != Mode::F) inv_eps = inv_eps_of<T>(a.eps);
     ChebK<T> ck = {T(0), T(0), T(0)};
     if (M == Mode::CHEB0 || M == Mode::CHEB || M == Mode::CHEBLAST) ck = cheb_of<T>(a.cheb, a.cheb_step);
     float red = 0.f;
-    for (int row = blockIdx.x; row < NP * NP; row += gridDim.x) {
-        const int Y = row % NP, Z = row / NP;
-        const bool yz_inner = Y > 0 && Y < n && Z > 0 && Z < n;
-        for (int X = threadIdx.x; X < NP; X += blockDim.x) {
-            const int idx = Z * sz + Y * sy + X;
-            const bool inner = yz_inner && X > 0 && X < n;
-            T val = T(0);
-            if (inner) {
-                // element with corner c = dx + 2 dy + 4 dz at this node: (X-dx, Y-dy, Z-dz)
-                const T* Cn = C + (Z * esz + Y * esy + X);
-                const T c0 = Cn[0], c1 = Cn[ne - 1];
-                const T c2 = Cn[2 * ne - esy], c3 = Cn[3 * ne - esy - 1];
-                const T c4 = Cn[4 * ne - esz], c5 = Cn[5 * ne - esz - 1];
-                const T c6 = Cn[6 * ne - esz - esy], c7 = Cn[7 * ne - esz - esy - 1];
-                val = (((c0 + c1) + (c2 + c3)) + ((c4 + c5) + (c6 + c7))) * a.node_scale;
-            }
-            if (ADJ)
-                epilogue_adj<T, M>(a, idx, inner, val, ck, red);
-            else
-                epilogue<T, M>(a, idx, inner, val, inv_eps, ck, red);
+    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < nodes; idx += gridDim.x * blockDim.x) {
+        const int X = idx % NP, YZ = idx / NP;
+        const int Y = YZ % NP, Z = YZ / NP;
+        const bool inner = X > 0 && X < n && Y > 0 && Y < n && Z > 0 && Z < n;
+        T val = T(0);
+        if (inner) {
+            // element with corner c = dx + 2 dy + 4 dz at this node: (X-dx, Y-dy, Z-dz)
+            const T* Cn = C + (Z * esz + Y * esy + X);
+            const T c0 = Cn[0], c1 = Cn[ne - 1];
+            const T c2 = Cn[2 * ne - esy], c3 = Cn[3 * ne - esy - 1];
+            const T c4 = Cn[4 * ne - esz], c5 = Cn[5 * ne - esz - 1];
+            const T c6 = Cn[6 * ne - esz - esy], c7 = Cn[7 * ne - esz - esy - 1];
+            val = (((c0 + c1) + (c2 + c3)) + ((c4 + c5) + (c6 + c7))) * a.node_scale;
         }
+        if (ADJ)
+            epilogue_adj<T, M>(a, idx, inner, val, ck, red);
+        else
+            epilogue<T, M>(a, idx, inner, val, inv_eps, ck, red);
     }
     stencil_reduce(a, red, red_sm);
 }
@@ -148,9 +147,9 @@ static jfnk_status launch_ep3d_pm(const StencilArgs<T>& a, cudaStream_t st) {
     const int bx = std::min(kEpElemThreads, ((g.n + 31) / 32) * 32);
     ep3d_elem_kernel<T, P, M, ADJ><<<dim3((g.n + bx - 1) / bx, g.n, g.n), bx, 0, st>>>(a);
     JFNK_LAUNCH_CHECK();
-    // the reduction scratch holds 2 kMaxRedBlocks partials: node rows grid-strided beyond
-    const long long rows = (long long)(g.n + 1) * (g.n + 1);
-    const int nb = (int)std::min<long long>(rows, 2LL * kMaxRedBlocks);
+    // the reduction scratch holds 2 kMaxRedBlocks partials: nodes grid-strided beyond
+    const long long nodes = (long long)(g.n + 1) * (g.n + 1) * (g.n + 1);
+    const int nb = (int)std::min<long long>((nodes + kEpNodeThreads - 1) / kEpNodeThreads, 2LL * kMaxRedBlocks);
     ep3d_node_kernel<T, M, ADJ><<<nb, kEpNodeThreads, 0, st>>>(a);
     JFNK_LAUNCH_CHECK();
     return JFNK_OK;

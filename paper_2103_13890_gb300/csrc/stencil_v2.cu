@@ -23,6 +23,7 @@
 #include <cstdio>
 
 #include "element.cuh"
+#include "pf2.cuh"
 #include "reduce.cuh"
 #include "stencil.cuh"
 #include "stencil_v2.cuh"
@@ -254,7 +255,6 @@ __global__ void __launch_bounds__(kV2Threads, 1) stencil3d_v2_kernel(const Stenc
     const int yA = y0 + w, yB = y0 + BY;
     const bool faceA = (w == 0) && y0 > 0;         // shared with the tile below
     const bool bndA = (yA == 0);
-    const bool faceB = yB < n;                      // shared with the tile above
     const bool bndB = yB == n;
     T carryA = T(0), carryB = T(0);
     float red = 0.f;
@@ -361,6 +361,235 @@ __global__ void __launch_bounds__(kV2Threads, 1) stencil3d_v2_kernel(const Stenc
         }
     }
     // block partial of the norm; the fixup kernel completes the reduction
+    if (a.red != RedOut::NONE) {
+        const double bs = block_sum(red, red_sm);
+        if (threadIdx.x == 0 && threadIdx.y == 0) a.partials[blockIdx.x + gridDim.x * blockIdx.y] = bs;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// FP32 variant with two elements per thread.  Thread (t, w) of an (n/2) x BY
+// CTA owns the elements with lower corners (2t, y0+w, k) and (2t+1, y0+w, k)
+// and evaluates both at once in the packed f32x2 form (pf2.cuh): the element
+// routine, the node-plane ring, the layer loop, the node totals and the face
+// buffer are those of the kernel above (same tiling, same fixup), with half
+// the threads and half the instructions per element.  Node rows in shared
+// memory have an even pitch, so the pair (2t, 2t+1) is one 8-byte word, and
+// the contributions of the corners with a = 1 (those to node x+1 of element
+// x) are stored one place to the right, so that the node pair (2t, 2t+1)
+// reads every corner of its 2^2 in-plane elements as one aligned pair.  The
+// per-node sums are added in the same order as above.
+// ---------------------------------------------------------------------------
+template <Prob P, Mode M, int MINB>
+__global__ void __launch_bounds__(kV3Threads, MINB) stencil3d_v3_kernel(const StencilArgs<float> a, const V2Geom q) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int n = q.n, BY = q.BY, NP = n + 2;
+    float* W = reinterpret_cast<float*>(smem_raw);  // [3][BY+1][NP]
+    float* C2 = W + 3 * (BY + 1) * NP;              // [2][8][BY][NP] (double-buffered by layer parity)
+    __shared__ double red_sm[32];
+    const Grid g = a.g;
+    const int sy32 = (int)g.sy, sz32 = (int)g.sz;
+    const int t = threadIdx.x, w = threadIdx.y;
+    const int x0 = 2 * t;
+    const int ty = blockIdx.x, c = blockIdx.y;
+    const int y0 = ty * BY;
+    const int z0 = c * q.ZC;
+    const int z1 = min(z0 + q.ZC, n);
+    float eps = 0.f, inv_eps = 0.f;
+    if (M != Mode::F) {
+        eps = eps_of2<float>(a.eps);
+        inv_eps = inv_eps_of2<float>(a.eps);
+    }
+    ChebK2<float> ck = {0.f, 0.f, 0.f};
+    if (M == Mode::CHEB0 || M == Mode::CHEB || M == Mode::CHEBLAST) ck = cheb_of2<float>(a.cheb, a.cheb_step);
+
+    auto node_val = [&](int x, int y, int z) -> float {
+        const int idx = z * sz32 + y * sy32 + x;
+        float val = a.u[idx];
+        if (M != Mode::F) {
+            const bool bnd = x == 0 || x == n || y == 0 || y == n || z == 0 || z == n;
+            if (!bnd) val += eps * a.v[idx];
+        }
+        return val;
+    };
+    // this thread's share of a plane: nodes (2t, 2t+1) of row y0+w, of row
+    // y0+BY (w == 0), and node n of those rows (last t)
+    const bool extra_row = (w == 0);
+    const bool extra_col = (x0 == n - 2);
+    // the next plane in registers: loaded at the start of a layer, stored to
+    // the ring after the layer's element arithmetic
+    float p0 = 0.f, p1 = 0.f, p2 = 0.f, p3 = 0.f, p4 = 0.f, p5 = 0.f;
+    auto load_plane = [&](int z, float& r0, float& r1, float& r2, float& r3, float& r4, float& r5) {
+        r0 = node_val(x0, y0 + w, z);
+        r1 = node_val(x0 + 1, y0 + w, z);
+        if (extra_col) r2 = node_val(n, y0 + w, z);
+        if (extra_row) {
+            r3 = node_val(x0, y0 + BY, z);
+            r4 = node_val(x0 + 1, y0 + BY, z);
+        }
+        if (extra_row && extra_col) r5 = node_val(n, y0 + BY, z);
+    };
+    auto store_plane = [&](int buf) {
+        float* Wb = W + buf * (BY + 1) * NP;
+        pf2_store(Wb + w * NP + x0, pf2_pack(p0, p1));
+        if (extra_col) Wb[w * NP + n] = p2;
+        if (extra_row) pf2_store(Wb + BY * NP + x0, pf2_pack(p3, p4));
+        if (extra_row && extra_col) Wb[BY * NP + n] = p5;
+    };
+
+    load_plane(z0, p0, p1, p2, p3, p4, p5);
+    store_plane(z0 % 3);
+    load_plane(z0 + 1, p0, p1, p2, p3, p4, p5);
+    store_plane((z0 + 1) % 3);
+
+    if (t == 0) {  // node 0 has no element on its left: its shifted a = 1 slots stay 0
+#pragma unroll
+        for (int b = 0; b < 2; ++b)
+#pragma unroll
+            for (int cc = 1; cc < 8; cc += 2) C2[((b * 8 + cc) * BY + w) * NP] = 0.f;
+    }
+    __syncthreads();
+
+    const int yA = y0 + w, yB = y0 + BY;
+    const bool faceA = (w == 0) && y0 > 0;  // shared with the tile below
+    const bool bndA = (yA == 0);
+    const bool bndB = yB == n;
+    pf2 carryA = pf2(0.0), carryB = pf2(0.0);
+    float red = 0.f;
+    const float scale = a.node_scale;
+    const ChebK2<float> ck0 = ck;
+    auto zero_node = [&](int idx) { epilogue2<float, M>(a, idx, false, 0.f, inv_eps, ck0, red); };
+
+    for (int k = z0; k < z1; ++k) {
+        float* C = C2 + (k & 1) * 8 * BY * NP;
+        const bool pf = (k + 2 <= z1);
+        if (pf) load_plane(k + 2, p0, p1, p2, p3, p4, p5);
+        // operands of this layer's node epilogue (complete nodes of row yA only)
+        const int idxA = k * sz32 + yA * sy32 + x0;
+        const bool rowComplete = !(k == 0 || bndA || faceA || k == z0);
+        EpiIn<float> e0, e1;
+        if (rowComplete && x0 > 0) epi_load<float, M>(a, idxA, e0);
+        if (rowComplete) epi_load<float, M>(a, idxA + 1, e1);
+        // corners of the element pair: a = 0 -> nodes (2t, 2t+1), a = 1 -> nodes (2t+1, 2t+2)
+        const float* W0 = W + (k % 3) * (BY + 1) * NP;
+        const float* W1 = W + ((k + 1) % 3) * (BY + 1) * NP;
+        pf2 ue[8];
+        {
+            const float* rows[4] = {W0 + w * NP + x0, W0 + (w + 1) * NP + x0, W1 + w * NP + x0,
+                                    W1 + (w + 1) * NP + x0};
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                ue[2 * i] = pf2_load(rows[i]);
+                float lo, hi;
+                pf2_unpack(ue[2 * i], lo, hi);
+                ue[2 * i + 1] = pf2_pack(hi, rows[i][2]);
+            }
+        }
+        pf2 r[8];
+        if (P == Prob::NDK3)
+            elem_nd3<pf2, true>(ue, pf2_load(a.kappa + (k * n + yA) * n + x0), r);
+        else
+            elem_nd3<pf2, false>(ue, pf2(1.0), r);
+        float* Cw = C + w * NP + x0;
+#pragma unroll
+        for (int cc = 0; cc < 8; cc += 2) pf2_store(Cw + cc * BY * NP, r[cc]);
+#pragma unroll
+        for (int cc = 1; cc < 8; cc += 2) {
+            float lo, hi;
+            pf2_unpack(r[cc], lo, hi);
+            Cw[cc * BY * NP + 1] = lo;
+            Cw[cc * BY * NP + 2] = hi;
+        }
+        // the ring slot of plane k+2 was last read by layer k-1 (before the
+        // previous barrier); the barrier below publishes it for layer k+1
+        if (pf) store_plane((k + 2) % 3);
+        __syncthreads();
+        // own row y0+w: b = 0 corners of element row w, b = 1 corners of row w-1
+        pf2 loA = pf2_load(Cw) + pf2_load(Cw + 1 * BY * NP);
+        pf2 hiA = pf2_load(Cw + 4 * BY * NP) + pf2_load(Cw + 5 * BY * NP);
+        if (w > 0) {
+            loA = loA + pf2_load(Cw + 2 * BY * NP - NP);
+            hiA = hiA + pf2_load(Cw + 6 * BY * NP - NP);
+            loA = loA + pf2_load(Cw + 3 * BY * NP - NP);
+            hiA = hiA + pf2_load(Cw + 7 * BY * NP - NP);
+        }
+        pf2 loB = pf2(0.0), hiB = pf2(0.0);
+        if (extra_row) {  // row y0+BY: b = 1 corners of element row BY-1
+            const float* Cb = C + (BY - 1) * NP + x0;
+            loB = pf2_load(Cb + 2 * BY * NP) + pf2_load(Cb + 3 * BY * NP);
+            hiB = pf2_load(Cb + 6 * BY * NP) + pf2_load(Cb + 7 * BY * NP);
+        }
+        // plane k
+        {
+            float v0, v1;
+            pf2_unpack(loA + carryA, v0, v1);
+            if (k == 0 || bndA) {
+                zero_node(idxA);
+                zero_node(idxA + 1);
+            } else if (faceA) {
+                if (x0 == 0) zero_node(idxA);
+                else a.face[ylo_idx(q, ty, c, k - z0, x0)] = v0;
+                a.face[ylo_idx(q, ty, c, k - z0, x0 + 1)] = v1;
+            } else if (k == z0) {
+                if (x0 == 0) zero_node(idxA);
+                else a.face[zlo_idx(q, ty, c, w, x0)] = v0;
+                a.face[zlo_idx(q, ty, c, w, x0 + 1)] = v1;
+            } else {
+                if (x0 == 0) zero_node(idxA);
+                else epilogue2_pf<float, M>(a, idxA, v0 * scale, inv_eps, ck0, e0, red);
+                epilogue2_pf<float, M>(a, idxA + 1, v1 * scale, inv_eps, ck0, e1, red);
+            }
+            if (extra_col) zero_node(idxA + 2);  // x = n
+            carryA = hiA;
+        }
+        if (extra_row) {
+            float v0, v1;
+            pf2_unpack(loB + carryB, v0, v1);
+            const int idx = k * sz32 + yB * sy32 + x0;
+            if (k == 0 || bndB) {
+                zero_node(idx);
+                zero_node(idx + 1);
+            } else {
+                if (x0 == 0) zero_node(idx);
+                else a.face[yhi_idx(q, ty, c, k - z0, x0)] = v0;
+                a.face[yhi_idx(q, ty, c, k - z0, x0 + 1)] = v1;
+            }
+            if (extra_col) zero_node(idx + 2);
+            carryB = hiB;
+        }
+    }
+    // plane z1: the carries are partial sums from the last layer only
+    {
+        float v0, v1;
+        pf2_unpack(carryA, v0, v1);
+        const int idx = z1 * sz32 + yA * sy32 + x0;
+        if (z1 == n || bndA) {
+            zero_node(idx);
+            zero_node(idx + 1);
+        } else if (faceA) {
+            if (x0 == 0) zero_node(idx);
+            else a.face[ylo_idx(q, ty, c, z1 - z0, x0)] = v0;
+            a.face[ylo_idx(q, ty, c, z1 - z0, x0 + 1)] = v1;
+        } else {
+            if (x0 == 0) zero_node(idx);
+            else a.face[zhi_idx(q, ty, c, w, x0)] = v0;
+            a.face[zhi_idx(q, ty, c, w, x0 + 1)] = v1;
+        }
+        if (extra_col) zero_node(idx + 2);
+        if (extra_row) {
+            pf2_unpack(carryB, v0, v1);
+            const int idxB = z1 * sz32 + yB * sy32 + x0;
+            if (z1 == n || bndB) {
+                zero_node(idxB);
+                zero_node(idxB + 1);
+            } else {
+                if (x0 == 0) zero_node(idxB);
+                else a.face[yhi_idx(q, ty, c, z1 - z0, x0)] = v0;
+                a.face[yhi_idx(q, ty, c, z1 - z0, x0 + 1)] = v1;
+            }
+            if (extra_col) zero_node(idxB + 2);
+        }
+    }
     if (a.red != RedOut::NONE) {
         const double bs = block_sum(red, red_sm);
         if (threadIdx.x == 0 && threadIdx.y == 0) a.partials[blockIdx.x + gridDim.x * blockIdx.y] = bs;
@@ -517,6 +746,78 @@ static jfnk_status launch_v2_pm(const StencilArgs<T>& a, cudaStream_t st) {
     stencil3d_fixup_kernel<T, M><<<fb, 256, 0, st>>>(a, q, main_blocks);
     JFNK_LAUNCH_CHECK();
     return JFNK_OK;
+}
+
+long long v3_face_count(const Grid& g, int max_threads, int ctas_per_sm) {
+    if (!v2_applicable(g)) return 0;
+    return v2_geometry(g, std::max(1, ctas_per_sm) * kNumSMs, max_threads).face_count;
+}
+
+template <Prob P, Mode M, int MINB>
+static jfnk_status launch_v3_pmb(const StencilArgs<float>& a, cudaStream_t st) {
+    // z chunks for MINB resident CTAs per SM
+    const V2Geom q = v2_geometry(a.g, MINB * kNumSMs, a.v2_threads);
+    if ((q.n / 2) * q.BY > kV3Threads) {
+        set_error("paired-element kernel: CTA of %d x %d threads", q.n / 2, q.BY);
+        return JFNK_ERR_INVALID_ARG;
+    }
+    if (q.face_count > a.face_cap) {
+        set_error("face scratch too small (%lld < %lld)", a.face_cap, q.face_count);
+        return JFNK_ERR_WORKSPACE;
+    }
+    const int main_blocks = q.Ty * q.Tz;
+    const int fb = fixup_blocks(q);
+    if (main_blocks + fb > kMaxRedBlocks * 2) {
+        set_error("v3 grid too large for the reduction scratch");
+        return JFNK_ERR_INVALID_ARG;
+    }
+    const size_t NP = (size_t)q.n + 2;
+    const size_t smem = sizeof(float) * (3 * (size_t)(q.BY + 1) * NP + 16 * (size_t)q.BY * NP);
+    static bool attr_set = false;
+    if (!attr_set) {
+        JFNK_CUDA_TRY(cudaFuncSetAttribute(stencil3d_v3_kernel<P, M, MINB>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024 / MINB));
+        JFNK_CUDA_TRY(cudaFuncSetAttribute(stencil3d_v3_kernel<P, M, MINB>,
+                                           cudaFuncAttributePreferredSharedMemoryCarveout, 100));
+        attr_set = true;
+    }
+    stencil3d_v3_kernel<P, M, MINB><<<dim3(q.Ty, q.Tz), dim3(q.n / 2, q.BY), smem, st>>>(a, q);
+    JFNK_LAUNCH_CHECK();
+    stencil3d_fixup_kernel<float, M><<<fb, 256, 0, st>>>(a, q, main_blocks);
+    JFNK_LAUNCH_CHECK();
+    return JFNK_OK;
+}
+
+// a.v3 = 1: one CTA per SM (up to 128 registers a thread); 2: two CTAs per SM
+// (64 registers; the Chebyshev modes spill 50-160 bytes a thread to local
+// memory); otherwise two for the residual, FD-action and b - Jv modes and one
+// for the Chebyshev modes, the faster choice for each on 129^3-257^3 grids.
+template <Prob P, Mode M>
+static jfnk_status launch_v3_pm(const StencilArgs<float>& a, cudaStream_t st) {
+    constexpr bool cheb = M == Mode::CHEB0 || M == Mode::CHEB || M == Mode::CHEBLAST;
+    const bool two = a.v3 == 2 || (a.v3 != 1 && !cheb);
+    return two ? launch_v3_pmb<P, M, 2>(a, st) : launch_v3_pmb<P, M, 1>(a, st);
+}
+
+template <Prob P>
+static jfnk_status launch_v3_p(Mode mode, const StencilArgs<float>& a, cudaStream_t st) {
+    switch (mode) {
+        case Mode::F: return launch_v3_pm<P, Mode::F>(a, st);
+        case Mode::JV: return launch_v3_pm<P, Mode::JV>(a, st);
+        case Mode::BMJ: return launch_v3_pm<P, Mode::BMJ>(a, st);
+        case Mode::CHEB0: return launch_v3_pm<P, Mode::CHEB0>(a, st);
+        case Mode::CHEB: return launch_v3_pm<P, Mode::CHEB>(a, st);
+        case Mode::CHEBLAST: return launch_v3_pm<P, Mode::CHEBLAST>(a, st);
+    }
+    set_error("unknown stencil mode");
+    return JFNK_ERR_INVALID_ARG;
+}
+
+jfnk_status launch_stencil_v3(Prob prob, Mode mode, const StencilArgs<float>& a, cudaStream_t st) {
+    if (prob == Prob::ND3) return launch_v3_p<Prob::ND3>(mode, a, st);
+    if (prob == Prob::NDK3) return launch_v3_p<Prob::NDK3>(mode, a, st);
+    set_error("v3 kernel is 3D only");
+    return JFNK_ERR_INVALID_ARG;
 }
 
 template <typename T, Prob P>

@@ -5,6 +5,7 @@
 namespace jfnk {
 
 constexpr int kV2Threads = 1024;  // at most n x BY threads per CTA
+constexpr int kV3Threads = 512;   // (n/2) x BY threads of the FP32 paired-element variant
 
 // Tiling of the halo-free 3D kernel and the layout of its face buffer.
 struct V2Geom {
@@ -25,5 +26,9 @@ long long v2_face_count(const Grid& g, int max_threads = kV2Threads);  // 0 if t
 
 template <typename T>
 jfnk_status launch_stencil_v2(Prob prob, Mode mode, const StencilArgs<T>& a, cudaStream_t st);
+// FP32 only: the same tiling and face fixup, two elements per thread in packed f32x2 arithmetic
+jfnk_status launch_stencil_v3(Prob prob, Mode mode, const StencilArgs<float>& a, cudaStream_t st);
+// face entries of that variant with ctas_per_sm resident CTAs per SM (0 if it does not apply)
+long long v3_face_count(const Grid& g, int max_threads, int ctas_per_sm);
 
 }  // namespace jfnk

@@ -5,7 +5,9 @@
 op: residual | jvp | smooth (one Chebyshev application = start + fused steps)
     | vcycle | solve (a whole JFNK-MG solve from u0 = 0 to 1e-8, preconditioner
     in --dtype) | batch (the batched solve of 64 uneven 2D Bratu instances,
-    sizes from {129^2, 257^2, 513^2} nodes, lambda ~ U[1, 6.5], seed 4).  Prints one JSON line with the mean time per call (CUDA events
+    sizes from {129^2, 257^2, 513^2} nodes, lambda ~ U[1, 6.5], seed 4)
+    | sweep (residual and FD action over grid sizes, FP64 and FP32).
+Prints one JSON line with the mean time per call (CUDA events
 on the current stream, after warm-up) and, for the element kernels, the
 achieved FP64/FP32 operation rate and HBM bandwidth of the algorithmic traffic.
 
@@ -27,7 +29,8 @@ def main():
     ap.add_argument("--kind", default="nd3d", choices=list(OPS_PER_ELEMENT))
     ap.add_argument("--n", type=int, default=128)
     ap.add_argument("--levels", type=int, default=0, help="0: coarsest level with 4 elements")
-    ap.add_argument("--op", default="residual", choices=["residual", "jvp", "smooth", "vcycle", "solve", "batch"])
+    ap.add_argument("--op", default="residual",
+                    choices=["residual", "jvp", "smooth", "vcycle", "solve", "batch", "sweep"])
     ap.add_argument("--dtype", default="f64", choices=["f64", "f32"])
     ap.add_argument("--reps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
@@ -36,6 +39,12 @@ def main():
     a = ap.parse_args()
     if a.op == "batch":
         return batch_main(a)
+    if a.op == "sweep":
+        return sweep_main(a)
+    print(json.dumps(run_one(a)))
+
+
+def run_one(a, restart=30):
     d = 2 if a.kind == "bratu2d" else 3
     n = a.n
     levels = a.levels
@@ -46,7 +55,7 @@ def main():
     dt = torch.float64 if a.dtype == "f64" else torch.float32
     o = jf.default_options(pc_dtype=jf.F64 if a.dtype == "f64" else jf.F32,
                            eps_mode_pc=jf.EPS_PAPER if a.dtype == "f64" else jf.EPS_FP32,
-                           nu_pre=2, nu_post=2, cheb_degree=4, rtol_newton=a.rtol)
+                           nu_pre=2, nu_post=2, cheb_degree=4, rtol_newton=a.rtol, restart=restart)
     kappa = None
     if a.kind == "ndk3d":
         g = torch.Generator().manual_seed(0)
@@ -110,7 +119,38 @@ def main():
         line["ops_per_s"] = OPS_PER_ELEMENT[a.kind] * elems * stencils / (ms * 1e-3)
     if words:
         line["gbs"] = words * w * nodes / (ms * 1e-3) / 1e9
-    print(json.dumps(line))
+    return line
+
+
+def sweep_main(a):
+    """Residual and FD-action throughput over grid sizes (where the roofline
+    bends): 3D nonlinear diffusion on 65^3 .. 513^3 nodes and 2D Bratu on
+    65^2 .. 4097^2 nodes, FP64 and FP32.  One JSON line per case with interior
+    DOF/s, the fraction of the measured HBM bandwidth taken by the algorithmic
+    bytes, and the fraction of the FP64 / FP32 pipe (152 SMs x 2 / 128
+    operations per clock x 2070 MHz) taken by the element arithmetic."""
+    import copy
+    import os
+    peaks = {}
+    pf = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "MEASURED_PEAKS.json")
+    if os.path.exists(pf):
+        with open(pf) as f:
+            peaks = json.load(f)
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    alu = {"f64": 152 * 2 * 2.07e9, "f32": 152 * 128 * 2.07e9}
+    cases = [("nd3d", n) for n in (64, 128, 256, 512)] + [("bratu2d", n) for n in (64, 256, 1024, 2048, 4096)]
+    for kind, n in cases:
+        for dt in ("f64", "f32"):
+            for op in ("residual", "jvp"):
+                b = copy.copy(a)
+                b.kind, b.n, b.levels, b.op, b.dtype, b.reps = kind, n, 0, op, dt, max(3, min(a.reps, 20))
+                line = run_one(b, restart=1)
+                d = 2 if kind == "bratu2d" else 3
+                line["dof_per_s"] = (n - 1) ** d / (line["ms"] * 1e-3)
+                line["pct_hbm"] = 100.0 * line["gbs"] / hbm
+                line["pct_alu"] = 100.0 * line["ops_per_s"] / alu[dt]
+                print(json.dumps(line), flush=True)
+                torch.cuda.empty_cache()
 
 
 def batch_main(a):

@@ -29,16 +29,23 @@ def rel(a, b):
 
 # 3D kernel selection (read when a Problem is created): "ep" runs the
 # element-parallel kernels on every 3D level, "tiled" the halo-free kernel
-# (n a multiple of 32, n >= 64) or the tiled one, "default" the library's choice.
+# (n a multiple of 32, n >= 64; in FP32 its two-elements-per-thread variant)
+# or the tiled one, "v2" the same with the one-element-per-thread halo-free
+# kernel in FP32 too, "default" the library's choice.
 KERNEL_PATHS = {
     "default": {},
     "ep": {"JFNK_EP3D_MAX_N_F64": "100000", "JFNK_EP3D_MAX_N_F32": "100000"},
     "tiled": {"JFNK_EP3D_MAX_N_F64": "0", "JFNK_EP3D_MAX_N_F32": "0"},
+    "v2": {"JFNK_EP3D_MAX_N_F64": "0", "JFNK_EP3D_MAX_N_F32": "0", "JFNK_V3_F32": "0"},
+    # the two-elements-per-thread kernel with one / two CTAs per SM in every
+    # mode (by default the Chebyshev modes take one and the others two)
+    "v3one": {"JFNK_EP3D_MAX_N_F64": "0", "JFNK_EP3D_MAX_N_F32": "0", "JFNK_V3_F32": "1"},
+    "v3two": {"JFNK_EP3D_MAX_N_F64": "0", "JFNK_EP3D_MAX_N_F32": "0", "JFNK_V3_F32": "2"},
 }
 
 
 def kernel_path(monkeypatch, path):
-    for k in ("JFNK_EP3D_MAX_N_F64", "JFNK_EP3D_MAX_N_F32"):
+    for k in ("JFNK_EP3D_MAX_N_F64", "JFNK_EP3D_MAX_N_F32", "JFNK_V3_F32"):
         monkeypatch.delenv(k, raising=False)
     for k, v in KERNEL_PATHS[path].items():
         monkeypatch.setenv(k, v)

@@ -141,23 +141,30 @@ def test_vcycle_parity_with_cgqn_coarse_solve(amp):
 def test_vcycle_near_the_solution_is_finite_and_of_the_oracles_size():
     """At the oracle's iterate after four Newton steps of the paper's solver at
     L2 (a twisted state where the shifted coarse CG of Alg. 1 is active), the
-    V-cycle is discontinuous in its input -- the oracle's own output moves by
-    O(1) under a 1e-13 perturbation of b (test_oracle_hyper) -- so GPU and
-    oracle outputs are compared by size only: finite, and within a factor 10."""
+    V-cycle is discontinuous in its input: the oracle's own output norm moves
+    by up to two orders of magnitude under 1e-13 relative perturbations of b
+    (test_oracle_hyper).  So GPU and oracle are compared by size only: the GPU
+    output is finite, zero on the Dirichlet faces, and its norm lies within a
+    factor 10 of the range the oracle spans over b and five such perturbations."""
     k, m = 2, 4
     lvs0 = jfnk.build_hyper_hierarchy(k)
     u, _ = jfnk.newton_solve(lvs0, hyper.boundary_state(m), jfnk.paper_options(max_newton=4))
     p = jf().Problem("beam3d", m, k + 1, options=jf().paper_options())
     p.mg_setup(dev(u), 0)
-    lvs = jfnk.build_hyper_hierarchy(k)
-    oo = jfnk.paper_options()
-    jfnk.setup_levels(lvs, u, oo, 0)
-    for l in range(1, k + 1):
-        lvs[l].lam_max = p.level_info(l)["lambda_max"]
+    lam = [p.level_info(l)["lambda_max"] for l in range(k + 1)]
     rng = np.random.default_rng(10)
     for _ in range(3):
         b = np.where(hyper.unknown_mask(u.shape), rng.normal(size=u.shape), 0.0)
         s = host(p.mg_vcycle(dev(b)))
-        so = jfnk.mg_vcycle(lvs, k, b, oo)
         assert np.all(np.isfinite(s))
-        assert 0.1 <= np.linalg.norm(s) / np.linalg.norm(so) <= 10.0
+        assert np.all(s[hyper.dirichlet_mask(u.shape)] == 0.0)
+        norms = []
+        for j in range(6):
+            lvs = jfnk.build_hyper_hierarchy(k)
+            oo = jfnk.paper_options()
+            jfnk.setup_levels(lvs, u, oo, 0)
+            for l in range(1, k + 1):
+                lvs[l].lam_max = lam[l]
+            rhs = b if j == 0 else b * (1.0 + 1e-13 * np.random.default_rng(100 + j).normal(size=b.shape))
+            norms.append(np.linalg.norm(jfnk.mg_vcycle(lvs, k, rhs, oo)))
+        assert 0.1 * min(norms) <= np.linalg.norm(s) <= 10.0 * max(norms), (np.linalg.norm(s), norms)

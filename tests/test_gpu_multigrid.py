@@ -136,6 +136,40 @@ def test_chebyshev_smoother_parity(kind, n, levels, path, nu, zero, monkeypatch)
     assert rel(host(s), so) <= _fd_tol(so, se)
 
 
+@pytest.mark.parametrize("path", ["default", "tiled", "v2", "v3two", "ep"])
+def test_chebyshev_smoother_fp32_3d(path, monkeypatch):
+    """FP32 smoothing on the finest level of a 65^3 hierarchy (on the "tiled"
+    path the two-elements-per-thread halo-free kernel, on "v2" the one-element
+    kernel, on "ep"/"default" the element-parallel kernels): every fused
+    Chebyshev mode against the oracle's FP64 smoother to FP32-FD accuracy, and
+    the FP32 kernels against each other to the FP32 FD round-off."""
+    kernel_path(monkeypatch, path)
+    n, levels = 64, 5
+    p, o, lv, oo, u = _setup_pair("nd3d", n, levels, pc="f32")
+    l = levels - 1
+    b = random_direction(n, 3, seed=31) * 1e-3
+    s0 = random_direction(n, 3, seed=32) * 1e-3
+    lam = p.level_info(l)["lambda_max"]
+    for zero, nu in ((True, 1), (False, 2)):
+        init = np.zeros_like(b) if zero else s0
+        s = dev(init, torch.float32)
+        p.smooth(dev(b, torch.float32), s, level=l, nu=nu, s_is_zero=zero)
+        so = jfnk.chebyshev(lv[l], init.copy(), lv[l].x, lv[l].Fx, b, nu, o.cheb_degree, lam, o.cheb_lo,
+                            o.cheb_hi, mode="fp32")
+        assert rel(host(s), so) <= 2e-3
+        _FP32_SMOOTH.setdefault((zero, nu), {})[path] = host(s)
+    # every path run so far in this session agrees to the FP32 FD round-off:
+    # each action carries ~2^-23 / sqrt(2^-23) = 3.5e-4 relative noise of its own
+    # rounding order, of which 1e-3 leaves room for a few actions
+    for runs in _FP32_SMOOTH.values():
+        ref = next(iter(runs.values()))
+        for other in runs.values():
+            assert rel(other, ref) <= 1e-3
+
+
+_FP32_SMOOTH = {}
+
+
 @pytest.mark.parametrize("kind,n,levels", [("bratu2d", 64, 4), ("nd3d", 32, 4)])
 def test_coarse_gmres_parity(kind, n, levels):
     p, o, lv, oo, u = _setup_pair(kind, n, levels)

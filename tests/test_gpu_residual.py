@@ -46,6 +46,11 @@ CASES = [("bratu2d", 7), ("bratu2d", 64), ("bratu2d", 95), ("bratu2d", 600),
          ("nd3d", 64), ("nd3d", 96), ("ndk3d", 64)]
 PATH_CASES = [(k, n, path) for k, n in CASES for path in ("default", "ep", "tiled")
               if k != "bratu2d" or path == "default"]
+# the FP32 one-element-per-thread halo-free kernel (the default FP32 kernel on
+# these grids evaluates two elements per thread), and the 129^3 grid in FP32
+PATH_CASES += [(k, n, path) for k, n in CASES for path in ("v2", "v3one")
+               if k != "bratu2d" and n % 32 == 0 and n >= 64]
+PATH_CASES += [("nd3d", 128, "default")]
 
 
 @functools.lru_cache(maxsize=None)
@@ -137,7 +142,8 @@ def test_jvp_fp64_parity(kind, n, path, monkeypatch):
 
 
 @pytest.mark.parametrize("kind,n,path", [("bratu2d", 64, "default"), ("nd3d", 33, "default"),
-                                         ("nd3d", 33, "tiled"), ("nd3d", 64, "default"), ("nd3d", 64, "ep")])
+                                         ("nd3d", 33, "tiled"), ("nd3d", 64, "default"), ("nd3d", 64, "ep"),
+                                         ("nd3d", 64, "tiled"), ("nd3d", 64, "v2"), ("nd3d", 96, "default")])
 def test_jvp_fp32_parity(kind, n, path, monkeypatch):
     """FP32 action with the single-precision step eps = sqrt(2^-23)(1+||u||)/||v||
     against the oracle's FP64 evaluation of the same quotient."""
