@@ -56,15 +56,7 @@ template jfnk_status launch_stencil2d_batched<float>(Mode, const StencilArgs<flo
 // ---------------------------------------------------------------------------
 // batched vector operations
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ bool b_inner(const Grid& g, long long i) {
-    const long long x = i % g.sy;
-    const long long yz = i / g.sy;
-    const long long y = yz % g.ny;
-    const long long z = yz / g.ny;
-    bool in = x > 0 && x < g.nx - 1 && y > 0 && y < g.ny - 1;
-    if (g.d == 3) in = in && z > 0 && z < g.nz - 1;
-    return in;
-}
+__device__ __forceinline__ bool b_inner(const Grid& g, long long i) { return grid_unknown(g, i); }
 
 __device__ __forceinline__ void b_finish_eps(const BVec& d, double nrm) {
     if (!d.slot) return;
@@ -146,10 +138,8 @@ __global__ void __launch_bounds__(kBThreads) bvec_kernel(const BVec* __restrict_
         const Grid gc = d.gc, gf = d.g;
         const T scale = (T)d.a;
         for (long long i = i0; i < gc.size; i += stride) {
-            const int x = (int)(i % gc.sy);
-            const long long yz = i / gc.sy;
-            const int y = (int)(yz % gc.ny);
-            const int z = (int)(yz / gc.ny);
+            int x, y, z;
+            grid_coords(gc, i, x, y, z);
             const bool bnd = x == 0 || x == gc.nx - 1 || y == 0 || y == gc.ny - 1 ||
                              (gc.d == 3 && (z == 0 || z == gc.nz - 1));
             const long long fc = (gc.d == 3 ? (long long)(2 * z) * gf.sz : 0) + (long long)(2 * y) * gf.sy + 2 * x;
@@ -169,8 +159,8 @@ __global__ void __launch_bounds__(kBThreads) bvec_kernel(const BVec* __restrict_
         const Grid gc = d.gc, gf = d.g;
         const T* c = (const T*)d.x;
         for (long long i = i0; i < gf.size; i += stride) {
-            const int x = (int)(i % gf.sy);
-            const int y = (int)(i / gf.sy);
+            int x, y, z;
+            grid_coords(gf, i, x, y, z);
             if (x == 0 || x == gf.nx - 1 || y == 0 || y == gf.ny - 1) continue;
             const int ix0 = x >> 1, ix1 = (x & 1) ? (x >> 1) + 1 : ix0;
             const int iy0 = y >> 1, iy1 = (y & 1) ? (y >> 1) + 1 : iy0;

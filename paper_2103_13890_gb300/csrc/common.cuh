@@ -63,8 +63,36 @@ struct Grid {
     }
 };
 
+// Node coordinates (x, y, z) of entry i of a scalar grid (nc = 1); 32-bit
+// index arithmetic where the grid allows it.
+__host__ __device__ __forceinline__ void grid_coords(const Grid& g, long long i, int& x, int& y, int& z) {
+    if (g.size <= 0x7fffffffLL) {
+        const unsigned int ii = (unsigned int)i, sy = (unsigned int)g.sy, ny = (unsigned int)g.ny;
+        const unsigned int yz = ii / sy, zz = yz / ny;
+        x = (int)(ii - yz * sy);
+        y = (int)(yz - zz * ny);
+        z = (int)zz;
+        return;
+    }
+    const long long yz = i / g.sy;
+    x = (int)(i - yz * g.sy);
+    y = (int)(yz % g.ny);
+    z = (int)(yz / g.ny);
+}
+
 // True for the entries that are unknowns (not Dirichlet data) of grid g.
 __host__ __device__ __forceinline__ bool grid_unknown(const Grid& g, long long i) {
+    if (g.size <= 0x7fffffffLL) {  // 32-bit index arithmetic (64-bit division is a long subroutine)
+        const unsigned int ii = (unsigned int)i;
+        const unsigned int node = g.nc == 1 ? ii : ii / (unsigned int)g.nc;
+        const unsigned int nx = (unsigned int)g.nx, ny = (unsigned int)g.ny;
+        const unsigned int yz = node / nx, x = node - yz * nx;
+        if (g.beam) return x > 0 && x < nx - 1;
+        const unsigned int z = yz / ny, y = yz - z * ny;
+        bool in = x > 0 && x < nx - 1 && y > 0 && y < ny - 1;
+        if (g.d == 3) in = in && z > 0 && z < (unsigned int)g.nz - 1;
+        return in;
+    }
     const long long node = g.nc == 1 ? i : i / g.nc;
     const long long x = node % g.nx;
     const long long yz = node / g.nx;

@@ -689,6 +689,8 @@ V2Geom v2_geometry(const Grid& g, int num_sms, int max_threads) {
     for (int tz = 1; tz <= g.n; ++tz) {
         const int zc = (g.n + tz - 1) / tz;
         if ((long long)(tz - 1) * zc >= g.n) continue;  // no empty chunk
+        // the block partials of the main and fixup kernels share 2 kMaxRedBlocks slots
+        if (tz > 1 && (long long)q.Ty * tz > 2 * kMaxRedBlocks - 4 * kNumSMs) break;
         const long long waves = ((long long)q.Ty * tz + num_sms - 1) / num_sms;
         const long long cost = waves * (zc + 1) * 16 + (tz - 1);  // small preference for fewer faces
         if (best_cost < 0 || cost < best_cost) {

@@ -26,10 +26,8 @@ __global__ void restrict_kernel(Grid gc, Grid gf, const T* __restrict__ f, T* __
                                 int inject_boundary) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < gc.size;
          i += (long long)gridDim.x * blockDim.x) {
-        const int x = (int)(i % gc.sy);
-        const long long yz = i / gc.sy;
-        const int y = (int)(yz % gc.ny);
-        const int z = (int)(yz / gc.ny);
+        int x, y, z;
+        grid_coords(gc, i, x, y, z);
         const bool bnd = x == 0 || x == gc.nx - 1 || y == 0 || y == gc.ny - 1 ||
                          (gc.d == 3 && (z == 0 || z == gc.nz - 1));
         const long long fc = (gc.d == 3 ? (long long)(2 * z) * gf.sz : 0) + (long long)(2 * y) * gf.sy + 2 * x;
@@ -75,10 +73,8 @@ template <typename T>
 __global__ void prolong_add_kernel(Grid gf, Grid gc, const T* __restrict__ c, T* __restrict__ s) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < gf.size;
          i += (long long)gridDim.x * blockDim.x) {
-        const int x = (int)(i % gf.sy);
-        const long long yz = i / gf.sy;
-        const int y = (int)(yz % gf.ny);
-        const int z = (int)(yz / gf.ny);
+        int x, y, z;
+        grid_coords(gf, i, x, y, z);
         const bool bnd = x == 0 || x == gf.nx - 1 || y == 0 || y == gf.ny - 1 ||
                          (gf.d == 3 && (z == 0 || z == gf.nz - 1));
         if (bnd) continue;
@@ -159,10 +155,8 @@ __global__ void mms_load_kernel(Grid g, const double* __restrict__ tab, double* 
     const double pi2 = 9.869604401089358;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < g.size;
          i += (long long)gridDim.x * blockDim.x) {
-        const int x = (int)(i % g.sy);
-        const long long yz = i / g.sy;
-        const int y = (int)(yz % g.ny);
-        const int z = (int)(yz / g.ny);
+        int x, y, z;
+        grid_coords(g, i, x, y, z);
         const bool bnd = x == 0 || x == g.nx - 1 || y == 0 || y == g.ny - 1 || z == 0 || z == g.nz - 1;
         double v = 0.0;
         if (!bnd) {
