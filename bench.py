@@ -47,6 +47,16 @@ METRIC = "JFNK-MG time to 1e-8 rel. residual; residual-eval DOF/s (%HBM), FP32 v
 ND_OPS_PER_ELEMENT = 164
 
 
+def max_over_ranks(dist, value):
+    """The largest value over the ranks of the process group: the job's time
+    is its slowest replica's (no data-path collective; one scalar)."""
+    import torch
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(value)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def load_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -427,9 +437,7 @@ def main():
     launches = jf.kernel_launches()
     ms = e0.elapsed_time(e1) / args.steps
     if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+        ms = max_over_ranks(dist, ms)
         dist.barrier()
     clocks = sampler.stop()
 
