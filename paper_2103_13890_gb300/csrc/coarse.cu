@@ -171,8 +171,10 @@ __device__ void coarse_apply_vjp(const Grid& g, const T* x, const T* v, T* elemC
 
 __device__ __forceinline__ bool coarse_inner(const Grid& g, long long i) { return grid_unknown(g, i); }
 
+// vsm: the Krylov basis V and the Hessenberg matrix H live in shared memory
+// (after the work arrays) instead of the global scratch a.V / a.H
 template <typename T, Prob P, bool ADJ>
-__device__ void coarse_gmres_body(const CoarseArgs<T>& a, unsigned char* smem_raw) {
+__device__ void coarse_gmres_body(const CoarseArgs<T>& a, unsigned char* smem_raw, bool vsm) {
     const Grid g = a.g;
     const int N = (int)g.size;
     const int ne = (int)g.elements();
@@ -193,8 +195,12 @@ __device__ void coarse_gmres_body(const CoarseArgs<T>& a, unsigned char* smem_ra
     const int tid = threadIdx.x;
     const int nwarps = blockDim.x >> 5;
     const int lane = tid & 31, wid = tid >> 5;
-    T* V = a.V;       // (m + 1) x N, global scratch
+    T* V = a.V;       // (m + 1) x N
     double* H = a.H;  // (m + 1) x m, column-major: H[j * (m+1) + i]
+    if (vsm) {
+        H = red + 32;
+        V = reinterpret_cast<T*>(H + (size_t)(m + 1) * m);
+    }
 
     // ||b|| over interior; V_0 = b / ||b||
     double acc = 0.0;
@@ -605,27 +611,38 @@ size_t coarse_cgqn_smem_bytes(const Grid& g, size_t esz) {
 }
 
 template <typename T, Prob P, bool ADJ>
-__global__ void __launch_bounds__(kCoarseThreads) coarse_gmres_kernel(CoarseArgs<T> a) {
+__global__ void __launch_bounds__(kCoarseThreads) coarse_gmres_kernel(CoarseArgs<T> a, int vsm) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    coarse_gmres_body<T, P, ADJ>(a, smem_raw);
+    coarse_gmres_body<T, P, ADJ>(a, smem_raw, vsm != 0);
 }
 
 // one CTA per instance of a batch (all instances share the coarse grid size)
 template <typename T, Prob P, bool ADJ>
-__global__ void __launch_bounds__(kCoarseThreads) coarse_gmres_batched_kernel(const CoarseArgs<T>* args) {
+__global__ void __launch_bounds__(kCoarseThreads) coarse_gmres_batched_kernel(const CoarseArgs<T>* args, int vsm) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const CoarseArgs<T> a = args[blockIdx.x];
-    coarse_gmres_body<T, P, ADJ>(a, smem_raw);
+    coarse_gmres_body<T, P, ADJ>(a, smem_raw, vsm != 0);
 }
 
+// Shared memory of the GMRES kernel: work arrays, plus V and H when vsm.
 template <typename T>
-size_t coarse_smem_bytes(const Grid& g, int maxit) {
+size_t coarse_smem_bytes(const Grid& g, int maxit, bool vsm) {
     const int ne = (int)g.elements();
     const int npe = coarse_npe(g);
     size_t b = sizeof(T) * (3 * (size_t)g.size + (size_t)ne * npe);
     b = (b + 15) & ~size_t(15);
     b += sizeof(double) * (4 * (size_t)maxit + 2 + 32);
+    if (vsm) b += sizeof(double) * (size_t)(maxit + 1) * maxit + sizeof(T) * (size_t)(maxit + 1) * g.size;
     return b;
+}
+
+// V and H go to shared memory when everything fits in kCoarseVsmBytes (the
+// basis is then read at shared-memory rather than L2 latency in the
+// orthogonalisation, the critical path of this one-CTA solver)
+constexpr size_t kCoarseVsmBytes = 160 * 1024;
+template <typename T>
+static bool coarse_vsm(const Grid& g, int maxit) {
+    return coarse_smem_bytes<T>(g, maxit, true) <= kCoarseVsmBytes;
 }
 
 template <typename T>
@@ -668,7 +685,8 @@ jfnk_status launch_coarse(Prob prob, const CoarseArgs<T>& a, cudaStream_t st) {
         return JFNK_ERR_INVALID_ARG;
     }
     if (a.method == 1) return launch_coarse_cgqn<T>(prob, a, st);
-    const size_t smem = coarse_smem_bytes<T>(a.g, a.maxit);
+    const bool vsm = coarse_vsm<T>(a.g, a.maxit);
+    const size_t smem = coarse_smem_bytes<T>(a.g, a.maxit, vsm);
     if (smem > 200 * 1024) {
         set_error("coarse solver shared memory %zu too large", smem);
         return JFNK_ERR_INVALID_ARG;
@@ -681,7 +699,7 @@ jfnk_status launch_coarse(Prob prob, const CoarseArgs<T>& a, cudaStream_t st) {
     do {                                                                                             \
         JFNK_CUDA_TRY(cudaFuncSetAttribute(coarse_gmres_kernel<T, PP, ADJ>,                           \
                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)); \
-        coarse_gmres_kernel<T, PP, ADJ><<<1, coarse_threads(a.g), smem, st>>>(a);                          \
+        coarse_gmres_kernel<T, PP, ADJ><<<1, coarse_threads(a.g), smem, st>>>(a, vsm ? 1 : 0);             \
     } while (0)
     switch (prob) {
         case Prob::BRATU2: JFNK_COARSE_LAUNCH(Prob::BRATU2, false); break;
@@ -716,10 +734,12 @@ jfnk_status launch_coarse_batched(const CoarseArgs<T>& a0, const CoarseArgs<T>* 
         set_error("batched coarse solve: 2D coarse grids within the single-CTA limits only");
         return JFNK_ERR_INVALID_ARG;
     }
-    const size_t smem = coarse_smem_bytes<T>(a0.g, a0.maxit);
+    const bool vsm = coarse_vsm<T>(a0.g, a0.maxit);
+    const size_t smem = coarse_smem_bytes<T>(a0.g, a0.maxit, vsm);
     JFNK_CUDA_TRY(cudaFuncSetAttribute(coarse_gmres_batched_kernel<T, Prob::BRATU2, false>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    coarse_gmres_batched_kernel<T, Prob::BRATU2, false><<<count, coarse_threads(a0.g), smem, st>>>(dev_args);
+    coarse_gmres_batched_kernel<T, Prob::BRATU2, false><<<count, coarse_threads(a0.g), smem, st>>>(dev_args,
+                                                                                                   vsm ? 1 : 0);
     JFNK_LAUNCH_CHECK();
     return JFNK_OK;
 }

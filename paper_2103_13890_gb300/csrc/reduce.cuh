@@ -43,6 +43,10 @@ __device__ __forceinline__ bool grid_sum_last_seg(double blocksum, double* parti
                                                   double* total, double* sm, unsigned int bid, unsigned int nb) {
     const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
     const int nt = blockDim.x * blockDim.y * blockDim.z;
+    if (nb == 1) {  // the only block: no partials, no completion counter
+        if (tid == 0) *total = blocksum;
+        return true;
+    }
     __shared__ int s_last;
     if (tid == 0) {
         partials[bid] = blocksum;

@@ -132,6 +132,90 @@ __global__ void __launch_bounds__(kEpNodeThreads) ep3d_node_kernel(const Stencil
     stencil_reduce(a, red, red_sm);
 }
 
+// FP32 levels with at most kEpSmallElems elements (n <= 8): both phases in one
+// CTA, the contributions exchanged through shared memory and the norm reduced
+// inside the block -- one launch and no grid-wide completion for the latency-
+// bound small levels.  Each element takes its 8 corners itself; the element
+// values and the per-node sums (same order) are those of the two kernels
+// above.  (In FP64 one SM would do all the element arithmetic on its two
+// FP64 lanes, which is slower than spreading it over the GPU.)
+constexpr int kEpSmallThreads = 512;
+constexpr int kEpSmallElems = 512;
+
+template <typename T, Prob P, Mode M, bool ADJ>
+__global__ void __launch_bounds__(kEpSmallThreads) ep3d_small_kernel(const StencilArgs<T> a) {
+    __shared__ T Cs[8 * kEpSmallElems];
+    __shared__ double red_sm[32];
+    const int n = a.g.n, NP = n + 1;
+    const int ne = n * n * n;
+    const int sy = (int)a.g.sy, sz = (int)a.g.sz;
+    T eps = T(0);
+    if (!ADJ && M != Mode::F) eps = eps_of<T>(a.eps);
+    for (int e = threadIdx.x; e < ne; e += blockDim.x) {
+        const int x = e % n, y = (e / n) % n, z = e / (n * n);
+        T ue[8], ve[8];
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            const int X = x + (c & 1), Y = y + ((c >> 1) & 1), Z = z + (c >> 2);
+            const int idx = Z * sz + Y * sy + X;
+            const bool bnd = X == 0 || X == n || Y == 0 || Y == n || Z == 0 || Z == n;
+            T uv = a.u[idx];
+            ve[c] = T(0);
+            if (ADJ) {
+                ve[c] = bnd ? T(0) : a.v[idx];
+            } else if (M != Mode::F) {
+                if (!bnd) uv += eps * a.v[idx];
+            }
+            ue[c] = uv;
+        }
+        T r[8];
+        if (ADJ) {
+            T dk;
+            elem_vjp3<T>(ue, ve, P == Prob::NDK3 ? a.kappa[e] : T(1), r, dk);
+            if (a.dkout) a.dkout[e] = dk * a.dk_scale;
+        } else if (P == Prob::NDK3) {
+            elem_nd3<T, true>(ue, a.kappa[e], r);
+        } else {
+            elem_nd3<T, false>(ue, T(1), r);
+        }
+#pragma unroll
+        for (int c = 0; c < 8; ++c) Cs[c * ne + e] = r[c];
+    }
+    __syncthreads();
+    T inv_eps = T(0);
+    if (!ADJ && M != Mode::F) inv_eps = inv_eps_of<T>(a.eps);
+    ChebK<T> ck = {T(0), T(0), T(0)};
+    if (M == Mode::CHEB0 || M == Mode::CHEB || M == Mode::CHEBLAST) ck = cheb_of<T>(a.cheb, a.cheb_step);
+    const int esy = n, esz = n * n;
+    float red = 0.f;
+    for (int idx = threadIdx.x; idx < NP * NP * NP; idx += blockDim.x) {
+        const int X = idx % NP, YZ = idx / NP;
+        const int Y = YZ % NP, Z = YZ / NP;
+        const bool inner = X > 0 && X < n && Y > 0 && Y < n && Z > 0 && Z < n;
+        T val = T(0);
+        if (inner) {
+            const T* Cn = Cs + (Z * esz + Y * esy + X);
+            const T c0 = Cn[0], c1 = Cn[ne - 1];
+            const T c2 = Cn[2 * ne - esy], c3 = Cn[3 * ne - esy - 1];
+            const T c4 = Cn[4 * ne - esz], c5 = Cn[5 * ne - esz - 1];
+            const T c6 = Cn[6 * ne - esz - esy], c7 = Cn[7 * ne - esz - esy - 1];
+            val = (((c0 + c1) + (c2 + c3)) + ((c4 + c5) + (c6 + c7))) * a.node_scale;
+        }
+        if (ADJ)
+            epilogue_adj<T, M>(a, idx, inner, val, ck, red);
+        else
+            epilogue<T, M>(a, idx, inner, val, inv_eps, ck, red);
+    }
+    if (a.red == RedOut::NONE) return;
+    const double bs = block_sum(red, red_sm);
+    if (threadIdx.x == 0) {
+        const double nrm = sqrt(bs);
+        if (a.red_norm) *a.red_norm = nrm;
+        if (a.red == RedOut::EPS || a.red == RedOut::EPS_UNIT)
+            set_eps_slot(a.red_eps, a.epsp, nrm, a.red == RedOut::EPS_UNIT, a.status);
+    }
+}
+
 template <typename T, Prob P, Mode M, bool ADJ>
 static jfnk_status launch_ep3d_pm(const StencilArgs<T>& a, cudaStream_t st) {
     const Grid& g = a.g;
@@ -142,6 +226,11 @@ static jfnk_status launch_ep3d_pm(const StencilArgs<T>& a, cudaStream_t st) {
     if (g.n > 1024) {
         set_error("element-parallel kernels: n = %d beyond 1024 (32-bit node indices, grid rows)", g.n);
         return JFNK_ERR_INVALID_ARG;
+    }
+    if (sizeof(T) == 4 && (long long)g.n * g.n * g.n <= kEpSmallElems) {
+        ep3d_small_kernel<T, P, M, ADJ><<<1, kEpSmallThreads, 0, st>>>(a);
+        JFNK_LAUNCH_CHECK();
+        return JFNK_OK;
     }
     // x-rows of up to 128 elements per block (a whole number of warps)
     const int bx = std::min(kEpElemThreads, ((g.n + 31) / 32) * 32);

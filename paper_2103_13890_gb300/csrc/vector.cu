@@ -6,10 +6,17 @@
 namespace jfnk {
 
 constexpr int kVecThreads = 256;
-constexpr int kVecBlocks = 304;  // 2 x 152 SMs; fixed so sums are reproducible
+// 8 x 152 SMs: every SM holds 2048 threads, so the streaming kernels keep
+// enough loads in flight to reach HBM speed (at 2 x 152 blocks a one-load-per-
+// iteration loop ran at ~0.6 TB/s); fixed, so sums are reproducible, and
+// within the 2 kMaxRedBlocks reduction partials
+constexpr int kVecBlocks = 1216;
+static_assert(kVecBlocks <= 2 * kMaxRedBlocks, "reduction partials");
 
+// about 8 entries a thread (loads in flight without a long tail of per-block
+// completions on short vectors), at most kVecBlocks blocks
 static int vec_blocks(long long len) {
-    long long b = (len + kVecThreads - 1) / kVecThreads;
+    long long b = (len + 8 * kVecThreads - 1) / (8 * kVecThreads);
     return (int)(b < kVecBlocks ? (b < 1 ? 1 : b) : kVecBlocks);
 }
 
@@ -21,11 +28,14 @@ __global__ void masked_stat_kernel(Grid g, const T* x, int what, double* out, do
                                    unsigned int* counter, EpsParams ep, EpsSlot* slot, double* norm_out) {
     __shared__ double sm[32];
     double acc = 0.0;
+    // unconditional loads (in bounds for every i), masked afterwards, so that
+    // the unrolled iterations keep several loads in flight
+#pragma unroll 4
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < g.size;
          i += (long long)gridDim.x * blockDim.x) {
-        if (!grid_inner(g, i)) continue;
-        double v = (double)x[i];
-        acc += (what == 0) ? fabs(v) : v * v;
+        const double v = (double)x[i];
+        const double t = (what == 0) ? fabs(v) : v * v;
+        if (grid_inner(g, i)) acc += t;
     }
     double bs = block_sum(acc, sm);
     double tot = 0.0;
@@ -362,10 +372,12 @@ __global__ void cheb_start_zero_kernel(Grid g, const T* __restrict__ b, T* __res
     __shared__ double sm[32];
     const double ti = cheb->theta_inv;
     double acc = 0.0;
+#pragma unroll 4
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < g.size;
          i += (long long)gridDim.x * blockDim.x) {
         const bool in = grid_inner(g, i);
-        const T bv = in ? b[i] : T(0);
+        T bv = b[i];  // loaded unconditionally (see masked_stat_kernel)
+        if (!in) bv = T(0);
         const T dv = (T)((double)bv * ti);
         r[i] = bv;
         d[i] = dv;
