@@ -76,7 +76,7 @@ FP64_INST_PER_CLK_SM = 2
 # DRAM bytes (read + write, cold cache) of one fused FP64 Chebyshev step at
 # 129^3 nodes, element + node phase, from the ncu capture summarised in
 # profiles/ep3d_fp64_cheb_n128_full.md (same kernels as timed here)
-EP_CHEB_N128_TRAFFIC = (33.851136 + 72.991488 + 198.790400 + 29.675520) * 1e6
+EP_CHEB_N128_TRAFFIC = (33.854720 + 72.553216 + 198.829312 + 28.200960) * 1e6
 
 
 def fp64_peak(peaks):
