@@ -152,7 +152,16 @@ void jfnk_default_options(jfnk_options* opts);
 void jfnk_paper_options(jfnk_options* opts);
 
 /* Create / destroy a problem description on the current CUDA device.
- * Allocates only host memory.  INVALID_ARG on bad kind/sizes/levels. */
+ * Allocates only host memory.  INVALID_ARG on bad kind/sizes/levels.
+ * The 3D kernel choice per level is read from the environment here; it
+ * changes speed only (results differ at rounding level):
+ *   JFNK_EP3D_MAX_N_F64 / _F32  levels with n <= this run the element-parallel
+ *                               kernels (defaults 2^20 / 64)
+ *   JFNK_V2_THREADS_F64 / _F32  CTA-size cap of the halo-free kernel (default
+ *                               1024; < 0: that kernel is not used)
+ *   JFNK_V3_F32                 FP32 halo-free levels: 0 one element a thread,
+ *                               1 / 2 two elements a thread with one / two CTAs
+ *                               per SM, 3 (default) two, CTAs chosen per mode */
 jfnk_status jfnk_problem_create(const jfnk_problem_desc* desc, jfnk_problem** out);
 jfnk_status jfnk_problem_destroy(jfnk_problem* p);
 
