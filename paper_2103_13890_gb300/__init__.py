@@ -11,6 +11,20 @@ if the library is missing.
     p = jf.Problem("bratu2d", n_elem=64, levels=4, lam=5.0)
     u = torch.zeros(65, 65, dtype=torch.float64, device="cuda")
     stats = p.solve(u)            # u now holds the discrete solution
+
+    # FP32 preconditioner inside the FP64 Newton/FGMRES loop
+    o = jf.default_options(nu_pre=2, nu_post=2, cheb_degree=4, rtol_newton=1e-8,
+                           pc_dtype=jf.F32, eps_mode_pc=jf.EPS_FP32)
+    q = jf.Problem("nd3d", 128, 6, options=o)
+
+    # the paper's own solver (outer CG, V(5,5), coarse CG with L-BFGS and the
+    # spectral shift) on the hyperelastic beam
+    b = jf.Problem("beam3d", 4, 3, options=jf.paper_options())
+
+The single operations (residual, jvp, smooth, transfer, coarse_solve,
+mg_setup, mg_vcycle, vjp) are methods of Problem; solve_batched solves many
+2D instances together; autograd.JFNKSolve differentiates a solve with respect
+to the coefficient field through the adjoint solve.
 """
 import ctypes
 
