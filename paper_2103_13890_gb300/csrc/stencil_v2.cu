@@ -378,7 +378,8 @@ __global__ void __launch_bounds__(kV2Threads, 1) stencil3d_v2_kernel(const Stenc
 // the contributions of the corners with a = 1 (those to node x+1 of element
 // x) are stored one place to the right, so that the node pair (2t, 2t+1)
 // reads every corner of its 2^2 in-plane elements as one aligned pair.  The
-// per-node sums are added in the same order as above.
+// per-node sums are added in the same order as above.  MINB: the CTAs per SM
+// the launch bounds provide for (1: up to 128 registers a thread, 2: 64).
 // ---------------------------------------------------------------------------
 template <Prob P, Mode M, int MINB>
 __global__ void __launch_bounds__(kV3Threads, MINB) stencil3d_v3_kernel(const StencilArgs<float> a, const V2Geom q) {
