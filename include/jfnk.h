@@ -326,7 +326,8 @@ jfnk_status jfnk_jvp_noalloc(int kind, int n_elem, double lambda, const void* ka
 const char* jfnk_last_error(void);
 
 /* Number of kernels this library launched on the calling thread since the last
- * reset (reset = 1 clears it).  Counts launches, not graph replays. */
+ * reset (returns the count; reset = 1 then clears it).  A replayed V-cycle
+ * graph adds the number of kernels it contains. */
 long long jfnk_kernel_launches(int reset);
 
 /* Event timing of the element-residual kernels, per kernel class (problem,

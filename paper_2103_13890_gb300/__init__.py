@@ -38,6 +38,7 @@ _LIB = None
 
 
 def lib():
+    """The loaded libjfnk.so (ctypes), loaded on first use; raises if it is missing."""
     global _LIB
     if _LIB is None:
         _LIB = _abi.load_library()
@@ -45,6 +46,8 @@ def lib():
 
 
 class JFNKError(RuntimeError):
+    """A jfnk_status other than OK, with the library's thread-local message."""
+
     def __init__(self, status, msg):
         super().__init__(f"{_abi.STATUS.get(status, status)}: {msg}")
         self.status = status
@@ -98,6 +101,7 @@ def _dtype_code(t):
 
 
 def stats_dict(s):
+    """jfnk_stats as a dict (histories cut to the iterations that ran)."""
     L = s.newton_its
     return {
         "newton_its": s.newton_its, "linear_its": s.linear_its, "status": _abi.STATUS.get(s.status, s.status),
@@ -149,6 +153,8 @@ class Problem:
         _check(lib().jfnk_set_workspace(self._h, opt_ref, _ptr(self.workspace), nbytes.value, _stream()))
 
     def shape(self, level=None):
+        """Shape of a node vector of a level (finest by default): (n+1,)*d, or
+        (m+1, m+1, 10m+1, 3) for the beam (axes z, y, x, component)."""
         lv = self.levels - 1 if level is None else level
         m = (self.n >> (self.levels - 1 - lv)) + 1
         if self.kind == "beam3d":
@@ -174,10 +180,15 @@ class Problem:
         return out
 
     def mg_setup(self, u, newton_step=0, options=None):
+        """Set up the hierarchy at the finest-level iterate u (FP64): projected
+        iterates x_l, A(x_l), the x statistics and the power-method estimates
+        lambda_l (random start at newton_step 0, warm start after), Sec. 2."""
         o = options or self.options
         _check(lib().jfnk_mg_setup(self._h, ctypes.byref(o), _ptr(u), int(newton_step), _stream()))
 
     def mg_vcycle(self, b, out=None, options=None):
+        """One V-cycle of Alg. 1 for J(u) s = b on the finest level (FP64 in and
+        out); requires mg_setup."""
         o = options or self.options
         out = torch.empty_like(b) if out is None else out
         _check(lib().jfnk_mg_vcycle(self._h, ctypes.byref(o), _ptr(b), _ptr(out), _stream()))
@@ -195,18 +206,23 @@ class Problem:
         return out
 
     def smooth(self, b, s, level=None, nu=1, s_is_zero=False, options=None):
+        """nu Chebyshev applications for J(x_l) s = b on a level, in place on s
+        (vectors in the preconditioner dtype); requires mg_setup."""
         o = options or self.options
         _check(lib().jfnk_smooth(self._h, ctypes.byref(o), self._lv(level), _ptr(b), _ptr(s), int(nu),
                                  1 if s_is_zero else 0, _stream()))
         return s
 
     def coarse_solve(self, b, out=None, options=None):
+        """The coarse-level solve of Alg. 1 (GMRES, or CG with L-BFGS and the
+        spectral shift) for J(x_0) s = b; requires mg_setup."""
         o = options or self.options
         out = torch.empty_like(b) if out is None else out
         _check(lib().jfnk_coarse_solve(self._h, ctypes.byref(o), _ptr(b), _ptr(out), _stream()))
         return out
 
     def level_info(self, level):
+        """lambda_max, sum |x_l| and ||x_l||_2 over the unknowns of a level."""
         lam, x1, x2 = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
         _check(lib().jfnk_level_info(self._h, level, ctypes.byref(lam), ctypes.byref(x1), ctypes.byref(x2),
                                      _stream()))
@@ -233,6 +249,8 @@ class Problem:
         return (out, dk) if dkappa else out
 
     def set_kappa(self, kappa):
+        """Replace the per-element coefficient of an NDK3D problem (copied to
+        the workspace and averaged onto the coarse levels)."""
         kappa = kappa.to(self.device, torch.float64).contiguous()
         self._keep.append(kappa)
         self._keep = self._keep[-2:]
@@ -261,6 +279,7 @@ class Problem:
         return d
 
     def close(self):
+        """Destroy the problem (host side; the workspace tensor is torch's)."""
         if self._h:
             lib().jfnk_problem_destroy(self._h)
             self._h = ctypes.c_void_p()
@@ -302,10 +321,14 @@ def jvp_noalloc(kind, u, Fu, v, lam=0.0, kappa=None, load=None, eps=0.0, eps_mod
 
 
 def kernel_launches(reset=False):
+    """Kernels the library has launched (graph replays count their kernels);
+    reset=True returns the count and restarts it."""
     return lib().jfnk_kernel_launches(1 if reset else 0)
 
 
 def profile_enable(on=True):
+    """Bracket every element-kernel launch with CUDA events on its stream (see
+    profile_read); V-cycles then launch directly instead of from their graph."""
     lib().jfnk_profile_enable(1 if on else 0)
 
 
