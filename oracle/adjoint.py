@@ -62,5 +62,7 @@ def adjoint_gradient(u, kappa, u_obs):
 
 
 def loss(u, u_obs):
+    """Misfit 1/2 ||u - u_obs||^2 over the interior nodes (the coefficient
+    problem's loss; the paper has no adjoint)."""
     mask = fem.interior(u.shape)
     return 0.5 * float(np.sum((u[mask] - u_obs[mask]) ** 2))

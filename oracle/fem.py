@@ -42,6 +42,8 @@ KINDS = ("bratu2d", "nd3d", "ndk3d", "minsurf2d")
 
 
 def dim_of(kind):
+    """Spatial dimension of a problem kind (Sec. 3: Bratu and the minimal
+    surface are 2D, nonlinear diffusion 3D)."""
     return 2 if kind in ("bratu2d", "minsurf2d") else 3
 
 
@@ -124,6 +126,7 @@ def boundary_mask(shape):
 
 
 def interior(shape):
+    """True at the unknowns: every node not on the Dirichlet boundary."""
     return ~boundary_mask(shape)
 
 

@@ -42,6 +42,7 @@ QP1 = np.array([0.5 - 0.5 * GAUSS_A, 0.5 + 0.5 * GAUSS_A])
 
 
 def shape_of(m):
+    """Node array shape of refinement level m = 2^k: (z, y, x, component)."""
     return (m + 1, m + 1, LENGTH * m + 1, 3)
 
 
@@ -70,6 +71,8 @@ def dirichlet_mask(shape):
 
 
 def unknown_mask(shape):
+    """True at the unknown components: every node with 0 < x < 10 (the lateral
+    faces are traction free, Sec. 3)."""
     return ~dirichlet_mask(shape)
 
 

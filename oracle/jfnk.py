@@ -80,6 +80,9 @@ EPS32 = 2.0 ** -23
 
 @dataclass
 class Options:
+    """Solver settings; the defaults are the 2D Bratu workload's (V(3,3),
+    degree 3 on [0.1, 1.1] lambda, 10 power iterations, FGMRES(30)) and
+    paper_options() gives the paper's own (Sec. 2, Sec. 3 "Setup")."""
     nu_pre: int = 3
     nu_post: int = 3
     cheb_degree: int = 3
@@ -125,6 +128,9 @@ def paper_options(**kw):
 # ---------------------------------------------------------------------------
 
 class Level:
+    """One level of the hierarchy (Sec. 2): the rediscretised operator on n
+    elements per direction, its current iterate x, F(x) and lambda_max."""
+
     def __init__(self, kind, n, lam, kappa, load):
         self.kind = kind
         self.n = n
@@ -229,6 +235,7 @@ def total_ge(levels):
 # ---------------------------------------------------------------------------
 
 def norm_i(v, mask):
+    """Euclidean norm over the unknowns."""
     return float(np.sqrt(np.sum(v[mask] ** 2)))
 
 
@@ -614,6 +621,7 @@ def backtrack(F_of, u, du, Fu, slope, c=1e-4, max_steps=10):
 
 @dataclass
 class Stats:
+    """Counts of one Newton solve: iterations, residual history and GE (Sec. 3)."""
     newton_its: int = 0
     linear_its: int = 0
     res_hist: list = field(default_factory=list)

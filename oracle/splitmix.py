@@ -30,6 +30,7 @@ M2 = np.uint64(0x94D049BB133111EB)
 
 
 def finalise(z):
+    """The SplitMix64 output function (Steele, Lea & Flood 2014) on uint64 z."""
     z = np.asarray(z, dtype=np.uint64)
     with np.errstate(over="ignore"):
         z = (z ^ (z >> np.uint64(30))) * M1
@@ -38,6 +39,7 @@ def finalise(z):
 
 
 def stream_key(seed, level):
+    """Key of the power-method start stream of a level: seed + level * constant."""
     with np.errstate(over="ignore"):
         return np.uint64(seed) + np.uint64(level) * LEVEL_MUL
 
