@@ -1,5 +1,6 @@
 // Element-parallel 3D element-residual kernels (two launches, no halo, no
-// barrier inside the element phase).
+// barrier inside the element phase; FP32 levels with at most 512 elements run
+// both phases in one CTA).
 #pragma once
 #include "stencil.cuh"
 
