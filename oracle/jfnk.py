@@ -584,16 +584,32 @@ def setup_levels(levels, u, opts, newton_step):
 # Line search and inexact Newton (Sec. 1 and Sec. 3 "Setup")
 # ---------------------------------------------------------------------------
 
-def backtrack(F_of, u, du, Fu, slope, c=1e-4, max_steps=10):
+def backtrack(F_of, u, du, Fu, slope, c=1e-4, max_steps=10, trials=None):
     """Backtracking on phi(alpha) = 1/2||F(u + alpha du)||^2 with quadratic and
-    cubic interpolation.  A trial step whose residual is not finite (e.g. an
-    inverted element of the hyperelastic beam, J <= 0) is cut to 0.1 alpha and
-    not used as an interpolation point.  Returns (alpha, F(u + alpha du), ok)."""
+    cubic interpolation (Dennis & Schnabel, Sec. 6.3).
+
+    The full step alpha = 1 is tried first.  A rejected trial is followed by the
+    minimiser of the quadratic through phi(0), phi'(0) = slope and the trial,
+    after that by the local minimiser of the cubic through phi(0), phi'(0) and
+    the last two trials; the new step is clipped to [0.1, 0.5] alpha.  A trial
+    whose residual is not finite (e.g. an inverted element of the hyperelastic
+    beam, J <= 0) is cut to 0.1 alpha and not used as an interpolation point.
+    At most max_steps residuals are evaluated.
+
+    Returns (alpha, F(u + alpha du), ok): the accepted step, or, when no trial
+    gave the sufficient decrease phi <= phi(0) + c alpha slope, the last
+    tested step with its own residual and ok = False.  The tested steps are
+    appended to `trials` when a list is given."""
     f0 = 0.5 * float(np.sum(Fu * Fu))
     alpha = 1.0
     prev_alpha = prev_f = None
+    Fn = None
+    tested = alpha
     for _ in range(max_steps):
         Fn = F_of(u + alpha * du)
+        tested = alpha
+        if trials is not None:
+            trials.append(alpha)
         fn = 0.5 * float(np.sum(Fn * Fn))
         if fn <= f0 + c * alpha * slope:
             return alpha, Fn, True
@@ -616,7 +632,7 @@ def backtrack(F_of, u, du, Fu, slope, c=1e-4, max_steps=10):
         t = min(max(t, 0.1 * alpha), 0.5 * alpha)
         prev_alpha, prev_f = alpha, fn
         alpha = t
-    return alpha, Fn, False
+    return tested, Fn, False
 
 
 @dataclass
@@ -626,6 +642,7 @@ class Stats:
     linear_its: int = 0
     res_hist: list = field(default_factory=list)
     alpha_hist: list = field(default_factory=list)
+    ls_hist: list = field(default_factory=list)
     lin_hist: list = field(default_factory=list)
     lam_hist: list = field(default_factory=list)
     ge: float = 0.0
@@ -649,6 +666,9 @@ def newton_solve(levels, u0, opts):
         if F0 == 0.0 or normF <= opts.rtol_newton * F0 or (opts.atol_newton > 0 and normF < opts.atol_newton):
             st.converged = True
             break
+        if not np.isfinite(normF):
+            st.status = "nonfinite"
+            break
         setup_levels(levels, u, opts, k)
         st.lam_hist.append([lv.lam_max for lv in levels[1:]])
         if opts.eta_mode == "paper":
@@ -667,9 +687,17 @@ def newton_solve(levels, u0, opts):
         st.lin_hist.append(its)
         if opts.line_search:
             slope = float(np.sum(F[fine.mask] * fd_jv(fine, u, F, du, "paper")[fine.mask]))
-            alpha, Fn, ok = backtrack(fine.F, u, du, F, slope, max_steps=opts.ls_max)
+            trials = []
+            alpha, Fn, ok = backtrack(fine.F, u, du, F, slope, max_steps=opts.ls_max, trials=trials)
+            st.ls_hist.append(len(trials))
             if not ok:
+                # no sufficient decrease: the step is not taken and the solve
+                # stops at the last accepted iterate (Dennis & Schnabel, Sec. 6.3)
                 st.status = "linesearch"
+                st.res_hist.append(normF)
+                st.alpha_hist.append(0.0)
+                st.newton_its = k + 1
+                break
         else:
             alpha, Fn = 1.0, fine.F(u + du)
         u = u + alpha * du
