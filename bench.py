@@ -22,7 +22,8 @@ extras:  also the same problem on 257^3 nodes, FP32 vs FP64 preconditioner,
          one, the forward + adjoint solve of the coefficient problem, and the
          paper's own solver variant on Bratu and the minimal surface at its
          refinement levels L1..L5.
-cpu_baseline / --impl reference: the CPU oracle timed on a bounded sample.
+cpu_baseline / --impl reference: the CPU oracle's complete solve of the same
+         problem at 33^3 nodes, timed on one host core.
 
 Multi-GPU (torchrun, N > 1): replicas only -- every rank solves its own
 instance, no collective on the data path; max-over-ranks time.
@@ -70,12 +71,13 @@ def load_peaks():
 # instructions (add, mul or fma) per clock per SM (the per-SM peak ncu reports
 # for sm__sass_thread_inst_executed_op_dfma_pred_on) x the maximum SM clock;
 # 0.629e12 instructions/s at 2070 MHz (the nominal 1.25 TFLOP/s counts an FMA
-# as two flops).
+# as two flops).  The roofline uses the rate measured by jfnk_measure_peaks and
+# reports this one beside it as a cross-check.
 GB300_SMS = 152
 FP64_INST_PER_CLK_SM = 2
-# DRAM bytes (read + write, cold cache) of one fused FP64 Chebyshev step at
-# 129^3 nodes, element + node phase, from the ncu capture summarised in
-# profiles/ep3d_fp64_cheb_n128_full.md (same kernels as timed here)
+# DRAM bytes (read + write) of one fused FP64 Chebyshev step at 129^3 nodes,
+# element + node phase: dram__bytes_read.sum + dram__bytes_write.sum of the two
+# kernels in one ncu capture of the same kernels (profiles/ holds the summary)
 EP_CHEB_N128_TRAFFIC = (33.854720 + 72.553216 + 198.829312 + 28.200960) * 1e6
 
 
@@ -134,54 +136,91 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # CPU oracle leg
 # ---------------------------------------------------------------------------
-def oracle_sample(n=N_ELEM, reps=2):
-    """Time the oracle's FD Jacobian action (= one gradient evaluation, GE) on
-    the full 129^3 workload, and its GE count for the whole solve from its own
-    JFNK-MG solve of the same problem at 17^3 nodes (GE is level-independent,
-    Sec. 3).  Estimated oracle time to solution = t_GE(129^3) x GE_solve."""
+ORACLE_N, ORACLE_LEVELS = 32, 4   # 33^3 nodes, 29,791 unknowns, coarse grid 4^3 elements as at 129^3
+
+
+def host_info():
+    """Host cores and CPU model of the machine the oracle runs on."""
+    import platform
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.split(":")[0].strip() in ("Model name", "Model"):
+                model = line.split(":", 1)[1].strip()
+                if line.startswith("Model name"):
+                    break
+    except Exception:
+        pass
+    return {"nproc": os.cpu_count(), "cpu_model": model, "machine": platform.machine()}
+
+
+def oracle_solve(n=ORACLE_N, levels=ORACLE_LEVELS):
+    """One complete oracle JFNK-MG solve of the bench problem at (n+1)^3 nodes
+    with the bench's settings (V(2,2), Chebyshev degree 4, 10 power
+    iterations, FGMRES(30), rtol 1e-8, u0 = 0, FP64); numpy on one thread.
+    Returns (seconds, stats)."""
     import numpy as np
 
     from oracle import fem, jfnk
-    from workloads import random_direction
-
     t0 = time.perf_counter()
-    lvs = jfnk.build_hierarchy("nd3d", 16, 3, load=fem.mms_load(16))
+    lv = jfnk.build_hierarchy("nd3d", n, levels, load=fem.mms_load(n))
     o = jfnk.Options(nu_pre=2, nu_post=2, cheb_degree=4, rtol_newton=1e-8)
-    _, st = jfnk.newton_solve(lvs, np.zeros((17,) * 3), o)
-    t_small = time.perf_counter() - t0
-    load = fem.mms_load(n)
-    lv = jfnk.Level("nd3d", n, 0.0, None, load)
-    u = np.zeros((n + 1,) * 3)
-    Fu = lv.F(u)
-    v = random_direction(n, 3, seed=1)
+    _, st = jfnk.newton_solve(lv, np.zeros((n + 1,) * 3), o)
+    return time.perf_counter() - t0, st
+
+
+def oracle_baseline(reps=2):
+    """cpu_baseline: the oracle's complete solve at 33^3 nodes, timed `reps`
+    times (best reported); the 129^3 figure beside it is an estimate that
+    scales by the unknowns (GE per solve is level-independent, Sec. 3)."""
     ts = []
     for _ in range(reps):
-        t1 = time.perf_counter()
-        jfnk.fd_jv(lv, u, Fu, v)
-        ts.append(time.perf_counter() - t1)
-    t_ge = min(ts)
-    return {"t_ge_s": t_ge, "ge_solve": st.ge, "estimate_s": t_ge * st.ge, "small_solve_s": t_small,
-            "sample": (f"{reps} oracle FD Jacobian actions (1 GE each) at 129^3 nodes, min {t_ge:.2f} s; "
-                       f"x GE={st.ge:.1f} of the oracle's own solve at 17^3 (level-independent count)")}
+        t, st = oracle_solve()
+        ts.append(t)
+    t = min(ts)
+    unknowns = (ORACLE_N - 1) ** 3
+    est = t * (N_ELEM - 1) ** 3 / unknowns
+    return {"value": t, "unit": "s", "cores": 1, "kind": "oracle", "threads": 1, **host_info(),
+            "sample": (f"complete oracle JFNK-MG solve of the same problem at {ORACLE_N + 1}^3 nodes "
+                       f"({unknowns} unknowns, {ORACLE_LEVELS} levels, same settings): {st.newton_its} Newton, "
+                       f"{st.linear_its} FGMRES, GE {st.ge:.1f}; best of {reps}: "
+                       + ", ".join(f"{x:.2f}" for x in ts) + " s"),
+            "workload": f"nd3d_{ORACLE_N + 1}^3_fp64_V(2,2)_cheb4_fgmres30_rtol1e-8",
+            "estimate_129_s": est,
+            "estimate_129_basis": "value x unknowns(129^3) / unknowns(33^3); an estimate, not a measurement"}
 
 
 def reference_arm(args):
+    """The oracle as the reference arm: every step is one complete oracle solve
+    of the bench problem at 33^3 nodes on one host core (the 129^3 solve takes
+    about 10 minutes on one core, too long for a step); the line reports the
+    measured seconds per 33^3 solve."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
-    steps = []
+    times, st = [], None
     for i in range(args.warmup + args.steps):
-        s = oracle_sample(reps=1)
+        t, st = oracle_solve()
         if i >= args.warmup:
-            steps.append(s)
-    est = statistics.mean(s["estimate_s"] for s in steps)
+            times.append(t)
+    val = statistics.mean(times)
+    wl = f"nd3d_{ORACLE_N + 1}^3_fp64_V(2,2)_cheb4_fgmres30_rtol1e-8"
+    unknowns = (ORACLE_N - 1) ** 3
+    sample = (f"per step one complete oracle JFNK-MG solve at {ORACLE_N + 1}^3 nodes ({unknowns} unknowns, "
+              f"{ORACLE_LEVELS} levels, the bench's settings): {st.newton_its} Newton, {st.linear_its} FGMRES, "
+              f"GE {st.ge:.1f}")
     line = {
-        "impl": "reference", "metric": METRIC, "value": est, "unit": "s", "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": est * 1e3, "higher_is_better": False,
+        "impl": "reference", "metric": METRIC, "value": val, "unit": "s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": val * 1e3, "higher_is_better": False,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (manufactured solution)",
-        "config": {"workload": WORKLOAD, "n_nodes": (N_ELEM + 1) ** 3},
-        "cpu_baseline": {"value": est, "unit": "s", "cores": 1, "kind": "oracle", "sample": steps[-1]["sample"]},
-        "e2e": {"value": est, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "config": {"workload": wl, "n_nodes": (ORACLE_N + 1) ** 3, "unknowns": unknowns,
+                   "note": "the oracle's solve of the bench problem at 33^3 nodes; the GPU arm's line is at 129^3"},
+        "cpu_baseline": {"value": val, "unit": "s", "cores": 1, "threads": 1, "kind": "oracle", "sample": sample,
+                         **host_info()},
+        "e2e": {"value": val, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "estimate_129_s": val * (N_ELEM - 1) ** 3 / unknowns,
+        "estimate_129_basis": "value x unknowns(129^3) / unknowns(33^3); an estimate, not a measurement",
     }
     print(json.dumps(line), flush=True)
     return 0
@@ -271,6 +310,34 @@ def adjoint_extra(jf, torch, n, shape, stream):
     return {"workload": "ndk3d 129^3, kappa = exp(GRF) seed 5, loss 1/2||u-u_obs||^2, FP32 PC, rtol 1e-8",
             "forward_s": ea.elapsed_time(eb) * 1e-3, "adjoint_s": eb.elapsed_time(ec) * 1e-3,
             "adjoint_fgmres_its": ast["linear_its"]}
+
+
+def bratu65_extra(jf, torch, stream, reps=5):
+    """2D Bratu lambda = 5 on 65^2 nodes, 4 levels, V(3,3) Chebyshev degree 3,
+    FGMRES(30), u0 = 0, to 1e-10 relative residual: time to solution with the
+    FP64 and the FP32 preconditioner (CUDA events, mean of `reps` solves after
+    two warm-ups)."""
+    out = {"workload": "bratu2d_65^2 lambda=5 V(3,3) cheb3 fgmres30 rtol1e-10, 4 levels", "unknowns": 63 ** 2}
+    for pc in ("f64", "f32"):
+        o = jf.default_options(rtol_newton=1e-10, pc_dtype=jf.F32 if pc == "f32" else jf.F64,
+                               eps_mode_pc=jf.EPS_FP32 if pc == "f32" else jf.EPS_PAPER)
+        p = jf.Problem("bratu2d", 64, 4, lam=5.0, options=o)
+        u = torch.zeros((65, 65), dtype=torch.float64, device="cuda")
+        for _ in range(2):
+            u.zero_()
+            p.solve(u)
+        torch.cuda.synchronize()
+        ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ea.record(stream)
+        for _ in range(reps):
+            u.zero_()
+            st = p.solve(u)
+        eb.record(stream)
+        torch.cuda.synchronize()
+        out[pc + "_pc_s"] = ea.elapsed_time(eb) / reps * 1e-3
+        out[pc + "_pc_its"] = {"newton": st["newton_its"], "fgmres": st["linear_its"], "ge": round(st["ge"], 1),
+                               "converged": bool(st["converged"])}
+    return out
 
 
 def large_extra(jf, torch, stream, hbm):
@@ -419,6 +486,8 @@ def main():
     for _ in range(args.warmup):
         st = solve_once(p64)
     torch.cuda.synchronize()
+    # measured FMA rates of this GPU (the ALU roofline denominators)
+    alu = jf.measure_peaks()
 
     # ---- timed region: K FP64 solves, inputs resident in HBM ------------------
     sampler = ClockSampler(local)
@@ -507,10 +576,17 @@ def main():
         t = ea.elapsed_time(eb) / reps * 1e-3
         w = 8 if name == "f64" else 4
         byts = 3 * w * N  # read u and the load, write F
+        ops = ND_OPS_PER_ELEMENT * n ** 3 / t
+        alu_peak = alu["fp64"] if name == "f64" else alu["fp32x2"]
         resid[name] = {"dof_per_s": dof / t, "ms": t * 1e3, "achieved_gbs": byts / t / 1e9,
-                       "pct_hbm": 100.0 * byts / t / 1e9 / hbm}
+                       "pct_hbm": 100.0 * byts / t / 1e9 / hbm, "alu_ops_per_s": ops,
+                       "pct_alu": 100.0 * ops / alu_peak,
+                       "alu_basis": (f"{ND_OPS_PER_ELEMENT} element operations x {n}^3 elements / time, of the "
+                                     + ("measured FP64 FMA rate" if name == "f64" else
+                                        "measured packed-FP32 (f32x2) FMA rate"))}
 
     # ---- batched workload and adjoint workload ---------------------------------
+    bratu65 = bratu65_extra(jf, torch, stream)
     batch = batched_extra(jf, torch)
     adj = adjoint_extra(jf, torch, n, shape, stream)
     paper = paper_variant_extra(jf, torch, stream)
@@ -524,22 +600,26 @@ def main():
         avg_s = tot / cnt * 1e-3
         ops = ND_OPS_PER_ELEMENT * elems
         achieved = ops / avg_s / 1e12
-        peak = fp64_peak(peaks) / 1e12
+        peak = alu["fp64"] / 1e12
+        derived = fp64_peak(peaks) / 1e12
         total_ms_all = sum(v[1] for v in prof.values())
         traffic = EP_CHEB_N128_TRAFFIC if name == "stencil_nd3d_f64_CHEB_n128" else None
         roof = {"kernel": name, "bound": "alu", "achieved": achieved, "peak": peak,
                 "unit": "Top/s (fp64 pipe)", "frac": achieved / peak, "traffic": traffic,
                 "traffic_unit": "bytes per fused step (element + node phase)",
+                "traffic_source": "ncu capture of the same two kernels at 129^3 (dram__bytes_read.sum + "
+                                  "dram__bytes_write.sum), not measured in this run",
+                "algorithmic_bytes": 8 * 8 * dof,
                 "avg_launch_ms": avg_s * 1e3, "launches": cnt,
                 "share_of_stencil_time": tot / total_ms_all if total_ms_all else None,
                 "timed_region": f"{args.steps} event-bracketed solves after the value's timed region "
                                 f"({ms_prof:.1f} ms per solve)",
-                "peak_source": "derived: 152 SMs x 2 FP64 inst/clk x max SM clock (bench.py fp64_peak)"}
+                "peak_source": "measured: jfnk_measure_peaks, FP64 FMA chains on every SM, in this run",
+                "peak_derived": derived, "frac_of_derived": achieved / derived}
 
     cpu = None
     if rank == 0 and world == 1:
-        s = oracle_sample(reps=2)
-        cpu = {"value": s["estimate_s"], "unit": "s", "cores": 1, "kind": "oracle", "sample": s["sample"]}
+        cpu = oracle_baseline(reps=2)
 
     st = stats[-1]
     if rank == 0:
@@ -557,6 +637,7 @@ def main():
                         "newton_its": st32["newton_its"], "fgmres_its": st32["linear_its"],
                         "rel_diff_vs_fp64_solution": sol_diff},
             "residual_eval": resid,
+            "bratu65": bratu65,
             "fp32_vs_fp64_pc_257": large,
             "batched": batch,
             "adjoint": adj,
@@ -564,7 +645,9 @@ def main():
             "e2e": {"value": e2e_ms * 1e-3, "unit": "s", "h2d_bytes_per_step": 8 * N, "d2h_bytes_per_step": 8 * N},
             "gpu_launches": int(launches),
             "roofline": roof,
-            "peaks": {"hbm_gbs": hbm, "source": peaks_src},
+            "peaks": {"hbm_gbs": hbm, "source": peaks_src, "fp64_fma_per_s": alu["fp64"],
+                      "fp32_fma_per_s": alu["fp32"], "fp32x2_fma_per_s": alu["fp32x2"],
+                      "fp64_derived_per_s": fp64_peak(peaks)},
             "cpu_baseline": cpu,
             "clocks": clocks,
         }

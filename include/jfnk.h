@@ -131,12 +131,18 @@ typedef struct {
     double alpha_hist[JFNK_MAX_HIST];    /* line-search steps */
     int lin_hist[JFNK_MAX_HIST];         /* FGMRES iterations per Newton step */
     double ge;                           /* GE = sum_l 2^(-d(L-l)) GE_l (Sec. 3) */
-    long long nF[JFNK_MAX_LEVELS];       /* residual evaluations per level (incl. FD actions) */
+    long long nF[JFNK_MAX_LEVELS];       /* residual evaluations per level (FD actions included) */
     double lambda_max[JFNK_MAX_LEVELS];  /* last power-method estimates */
     double setup_ms, solve_ms;
     int coarse_shifts;                   /* shifted coarse CG calls (Alg. 1 while-loop) */
     int coarse_negcurv;                  /* coarse CG calls ended by negative curvature */
     int outer_negcurv;                   /* outer CG solves ended by negative curvature */
+    long long nJv[JFNK_MAX_LEVELS];      /* FD Jacobian actions per level (part of nF; the
+                                            coarse Krylov iterations count on level 0) */
+    int ls_hist[JFNK_MAX_HIST];          /* residual evaluations of the line search per Newton
+                                            step; when none gives a sufficient decrease the
+                                            step is not taken (alpha_hist 0, u and ||F||
+                                            unchanged) and the solve returns JFNK_ERR_LINESEARCH */
 } jfnk_stats;
 
 /* Defaults of the 2D Bratu workload: V(3,3), degree 3, [0.1, 1.1] lambda_max,
@@ -324,6 +330,15 @@ jfnk_status jfnk_jvp_noalloc(int kind, int n_elem, double lambda, const void* ka
 
 /* Message for the last error on the calling thread. */
 const char* jfnk_last_error(void);
+
+/* Measured arithmetic peaks of the current GPU (the paper has no counterpart;
+ * these are the denominators of the element kernels' ALU rooflines): FMA
+ * operations per second of independent FMA chains on every SM, FP64, FP32, and
+ * FP32 in the packed fma.rn.f32x2 form (two FMAs per instruction).  Any output
+ * pointer may be NULL to skip that measurement.  Host pointers; launches a few
+ * 5-20 ms kernels on `stream` and synchronises it.  Allocates nothing. */
+jfnk_status jfnk_measure_peaks(double* fp64_fma_per_s, double* fp32_fma_per_s, double* fp32x2_fma_per_s,
+                               void* stream);
 
 /* Number of kernels this library launched on the calling thread since the last
  * reset (returns the count; reset = 1 then clears it).  A replayed V-cycle

@@ -53,6 +53,11 @@ class JFNKError(RuntimeError):
         self.status = status
 
 
+def last_error():
+    """The library's message for the last error on the calling thread."""
+    return lib().jfnk_last_error().decode()
+
+
 def _check(status):
     if status != 0:
         raise JFNKError(status, lib().jfnk_last_error().decode())
@@ -107,8 +112,9 @@ def stats_dict(s):
         "newton_its": s.newton_its, "linear_its": s.linear_its, "status": _abi.STATUS.get(s.status, s.status),
         "converged": bool(s.converged), "res_hist": list(s.res_hist[:L + 1]),
         "alpha_hist": list(s.alpha_hist[:L]), "lin_hist": list(s.lin_hist[:L]), "ge": s.ge,
-        "nF": list(s.nF), "lambda_max": list(s.lambda_max), "solve_ms": s.solve_ms,
+        "nF": list(s.nF), "nJv": list(s.nJv), "lambda_max": list(s.lambda_max), "solve_ms": s.solve_ms,
         "coarse_shifts": s.coarse_shifts, "coarse_negcurv": s.coarse_negcurv, "outer_negcurv": s.outer_negcurv,
+        "ls_hist": list(s.ls_hist[:L]),
     }
 
 
@@ -318,6 +324,14 @@ def jvp_noalloc(kind, u, Fu, v, lam=0.0, kappa=None, load=None, eps=0.0, eps_mod
     _check(lib().jfnk_jvp_noalloc(KINDS[kind], n, float(lam), kp, lp, _dtype_code(u), _ptr(u), _ptr(Fu), _ptr(v),
                                   _ptr(out), float(eps), int(eps_mode), _stream()))
     return out
+
+
+def measure_peaks():
+    """Measured FMA/s of the current GPU: {"fp64", "fp32", "fp32x2"} (FMA chains
+    on every SM, jfnk_measure_peaks)."""
+    a, b, c = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    _check(lib().jfnk_measure_peaks(ctypes.byref(a), ctypes.byref(b), ctypes.byref(c), _stream()))
+    return {"fp64": a.value, "fp32": b.value, "fp32x2": c.value}
 
 
 def kernel_launches(reset=False):

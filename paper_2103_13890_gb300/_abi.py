@@ -45,7 +45,8 @@ class Stats(ctypes.Structure):
                 ("ge", ctypes.c_double), ("nF", ctypes.c_longlong * MAX_LEVELS),
                 ("lambda_max", ctypes.c_double * MAX_LEVELS), ("setup_ms", ctypes.c_double),
                 ("solve_ms", ctypes.c_double), ("coarse_shifts", ctypes.c_int),
-                ("coarse_negcurv", ctypes.c_int), ("outer_negcurv", ctypes.c_int)]
+                ("coarse_negcurv", ctypes.c_int), ("outer_negcurv", ctypes.c_int),
+                ("nJv", ctypes.c_longlong * MAX_LEVELS), ("ls_hist", ctypes.c_int * MAX_HIST)]
 
 
 # (name, restype, argtypes) of every exported symbol declared in include/jfnk.h
@@ -75,6 +76,7 @@ SIGNATURES = [
     ("jfnk_vjp", _i, [_vp, _i, _i, _vp, _vp, _vp, _vp, _vp]),
     ("jfnk_set_kappa", _i, [_vp, _vp, _vp]),
     ("jfnk_adjoint_solve", _i, [_vp, ctypes.POINTER(Options), _vp, _vp, _vp, _vp, _d, ctypes.POINTER(Stats), _vp]),
+    ("jfnk_measure_peaks", _i, [ctypes.POINTER(_d), ctypes.POINTER(_d), ctypes.POINTER(_d), _vp]),
     ("jfnk_profile_enable", None, [_i]),
     ("jfnk_profile_read", _i, [_i, ctypes.c_char_p, _i, ctypes.POINTER(ctypes.c_longlong),
                                ctypes.POINTER(_d), ctypes.POINTER(_d)]),

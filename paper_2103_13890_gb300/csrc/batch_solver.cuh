@@ -537,6 +537,7 @@ static jfnk_status bresidual64(BCtx& b, const std::vector<int>& S, const std::ve
         args.push_back(a);
         gs.push_back(p.lv[p.L].g);
         p.nF[p.L]++;
+        p.nFplain[p.L]++;
     }
     jfnk_status err = JFNK_OK;
     const TileCfg& tc = b.tile[1];
@@ -625,6 +626,7 @@ static jfnk_status bsetup(BCtx& b, const std::vector<int>& S, int newton_step) {
             a.out = as<T>(p.lv[c].Ax);
             args.push_back(a);
             p.nF[c]++;
+            p.nFplain[c]++;
             xv.push_back(p.lv[c].x);
             o1.push_back(p.lv[c].xstat_paper);
             o2.push_back(p.lv[c].xstat_fp32);
@@ -906,9 +908,14 @@ static jfnk_status bfgmres(BCtx& b, const std::vector<int>& S, const std::vector
         for (int i : act) {
             std::vector<double> y(k[i]);
             for (int q = k[i] - 1; q >= 0; --q) {
+                const double hqq = H[i][(size_t)q * (m + 1) + q];
+                if (hqq == 0.0) {
+                    set_error("FGMRES breakdown in instance %d: singular Hessenberg matrix at column %d", i, q);
+                    return JFNK_ERR_BREAKDOWN;
+                }
                 double t = g[i][q];
                 for (int r = q + 1; r < k[i]; ++r) t -= H[i][(size_t)r * (m + 1) + q] * y[r];
-                y[q] = t / H[i][(size_t)q * (m + 1) + q];
+                y[q] = t / hqq;
             }
             for (int q = 0; q < k[i]; ++q) yall[(size_t)i * kResStride + 1 + q] = y[q];
         }
@@ -1082,7 +1089,7 @@ static jfnk_status bsolve(BCtx& b, jfnk_stats* stats) {
     std::vector<int> all(B);
     for (int i = 0; i < B; ++i) {
         all[i] = i;
-        for (int l = 0; l <= b.ps[i]->L; ++l) b.ps[i]->nF[l] = 0;
+        for (int l = 0; l <= b.ps[i]->L; ++l) b.ps[i]->nF[l] = b.ps[i]->nFplain[l] = 0;
     }
     std::vector<long long> ci0(B, 0);
     for (int i = 0; i < B; ++i)
@@ -1182,6 +1189,8 @@ static jfnk_status bsolve(BCtx& b, jfnk_stats* stats) {
         }
         std::vector<int> search = act;
         std::vector<char> ok(B, 0);
+        std::vector<int> trials(B, 0);
+        std::vector<double> tested(B, 1.0);
         for (int ls = 0; ls < (o.line_search ? o.ls_max : 1) && !search.empty(); ++ls) {
             std::vector<double*> ut;
             std::vector<const double*> uu, dd;
@@ -1200,6 +1209,8 @@ static jfnk_status bsolve(BCtx& b, jfnk_stats* stats) {
             std::vector<int> again;
             for (int i : search) {
                 nT[i] = hr[(size_t)i * kResStride];
+                trials[i]++;
+                tested[i] = alpha[i];
                 const double f0 = 0.5 * nF[i] * nF[i];
                 const double fn = 0.5 * nT[i] * nT[i];
                 if (!o.line_search || (std::isfinite(fn) && fn <= f0 + 1e-4 * alpha[i] * slope[i])) {
@@ -1208,7 +1219,11 @@ static jfnk_status bsolve(BCtx& b, jfnk_stats* stats) {
                 }
                 double t;
                 if (!std::isfinite(fn)) {
-                    t = 0.1 * alpha[i];
+                    // cut the step; the trial is not an interpolation point
+                    alpha[i] = 0.1 * alpha[i];
+                    pa[i] = -1.0;
+                    again.push_back(i);
+                    continue;
                 } else if (pa[i] < 0.0) {
                     t = -slope[i] * alpha[i] * alpha[i] / (2.0 * (fn - f0 - slope[i] * alpha[i]));
                 } else {
@@ -1231,28 +1246,38 @@ static jfnk_status bsolve(BCtx& b, jfnk_stats* stats) {
             }
             search = again;
         }
-        // accept the last trial of every instance
-        {
+        // take the accepted trial of every instance; an instance whose line
+        // search found no sufficient decrease keeps its iterate and stops
+        // (Dennis & Schnabel, Sec. 6.3)
+        std::vector<int> take;
+        for (int i : act)
+            if (ok[i]) take.push_back(i);
+        if (!take.empty()) {
             std::vector<double*> uo;
             std::vector<const double*> ut;
-            for (int i : act) {
+            for (int i : take) {
                 uo.push_back(b.u[i]);
                 ut.push_back(b.ps[i]->utrial);
             }
-            JFNK_TRY(baxpby(b, act, uo, ut, std::vector<double>(act.size(), 1.0), std::vector<double>(act.size(), 0.0)));
+            JFNK_TRY(baxpby(b, take, uo, ut, std::vector<double>(take.size(), 1.0),
+                            std::vector<double>(take.size(), 0.0)));
         }
         for (int i : act) {
             P& p = *b.ps[i];
+            S[i].newton_its = k + 1;
+            if (k < JFNK_MAX_HIST) S[i].ls_hist[k] = trials[i];
+            if (!ok[i]) {
+                failed[i] = 1;
+                S[i].status = JFNK_ERR_LINESEARCH;
+                if (k + 1 < JFNK_MAX_HIST) S[i].res_hist[k + 1] = nF[i];
+                if (k < JFNK_MAX_HIST) S[i].alpha_hist[k] = 0.0;
+                continue;
+            }
             std::swap(p.F64, p.Ftrial);
             std::swap(p.Au64, p.Autrial);
             nF[i] = nT[i];
-            S[i].newton_its = k + 1;
             if (k + 1 < JFNK_MAX_HIST) S[i].res_hist[k + 1] = nF[i];
-            if (k < JFNK_MAX_HIST) S[i].alpha_hist[k] = alpha[i];
-            if (o.line_search && !ok[i]) {
-                failed[i] = 1;
-                S[i].status = JFNK_ERR_LINESEARCH;
-            }
+            if (k < JFNK_MAX_HIST) S[i].alpha_hist[k] = tested[i];
         }
     }
     jfnk_status result = JFNK_OK;
@@ -1265,6 +1290,7 @@ static jfnk_status bsolve(BCtx& b, jfnk_stats* stats) {
         double ge = 0.0;
         for (int l = 0; l <= p.L && l < JFNK_MAX_LEVELS; ++l) {
             S[i].nF[l] = p.nF[l];
+            S[i].nJv[l] = p.nF[l] - p.nFplain[l];
             ge += std::pow(2.0, -2.0 * (p.L - l)) * (double)p.nF[l];
             if (l >= 1) JFNK_CUDA_TRY(cudaMemcpy(&S[i].lambda_max[l], p.lv[l].lam, sizeof(double), cudaMemcpyDeviceToHost));
         }

@@ -125,8 +125,10 @@ struct jfnk_problem {
     long long vgraph_key[16] = {0};
     long long vgraph_nF[JFNK_MAX_LEVELS] = {0};
     long long vgraph_launches = 0;
-    // host counters
+    // host counters: residual evaluations per level (FD actions included) and,
+    // among them, the plain evaluations F(x) (the rest are FD actions)
     long long nF[JFNK_MAX_LEVELS];
+    long long nFplain[JFNK_MAX_LEVELS];
 };
 
 namespace jfnk {
@@ -526,6 +528,7 @@ static jfnk_status mg_setup_T(P& p, const jfnk_options& o, const double* u, int 
         a.out = as<T>(L.Ax);
         JFNK_TRY(launch_stencil<T>(prob_of(p), Mode::F, a, st));
         p.nF[l]++;
+        p.nFplain[l]++;
         JFNK_TRY(masked_stat<T>(L.g, as<T>(L.x), 0, L.xstat_paper, p.red, st));
         JFNK_TRY(masked_stat<T>(L.g, as<T>(L.x), 1, L.xstat_fp32, p.red, st));
     }
@@ -615,6 +618,7 @@ static jfnk_status residual64(P& p, const double* u, double* F, double* Au, cuda
     a.load = p.load64;
     a.load_const = (p.desc.kind == JFNK_NDK3D) ? std::pow(p.lv[p.L].h, 3) : 0.0;
     p.nF[p.L]++;
+    p.nFplain[p.L]++;
     return launch_stencil<double>(prob_of(p), Mode::F, a, st);
 }
 
@@ -750,11 +754,19 @@ static jfnk_status fgmres(P& p, const jfnk_options& o, const double* u, double e
             }
             JFNK_TRY(scale_by_inv(p.V64 + (size_t)(j + 1) * N, p.w64, N, p.hbuf + 2 * (m + 2), st));
         }
-        // y = H^-1 g, delta += Z y
+        // y = H^-1 g, delta += Z y.  A zero diagonal entry of the rotated
+        // Hessenberg matrix means the Krylov space stopped growing with the
+        // preconditioned direction mapped to zero (J z_j = 0 in its span): the
+        // least-squares problem is singular and there is no update to take.
         for (int i = k - 1; i >= 0; --i) {
+            const double hii = H[(size_t)i * (m + 1) + i];
+            if (hii == 0.0) {
+                set_error("FGMRES breakdown: singular Hessenberg matrix at column %d (residual %.3e)", i, res);
+                return JFNK_ERR_BREAKDOWN;
+            }
             double t = gv[i];
             for (int q = i + 1; q < k; ++q) t -= H[(size_t)q * (m + 1) + i] * y[q];
-            y[i] = t / H[(size_t)i * (m + 1) + i];
+            y[i] = t / hii;
         }
         JFNK_CUDA_TRY(cudaMemcpyAsync(p.ydev, y.data(), sizeof(double) * k, cudaMemcpyHostToDevice, st));
         JFNK_TRY(combine<T>(p.delta, Z, N, N, k, p.ydev, st));
@@ -867,7 +879,7 @@ static jfnk_status solve_T(P& p, const jfnk_options& o, double* u, jfnk_stats* s
     const long long N = g.size;
     jfnk_stats S;
     memset(&S, 0, sizeof(S));
-    for (int l = 0; l <= p.L; ++l) p.nF[l] = 0;
+    for (int l = 0; l <= p.L; ++l) p.nF[l] = p.nFplain[l] = 0;
     long long ci0 = 0;
     JFNK_CUDA_TRY(cudaMemcpyAsync(&ci0, p.coarse_iters, sizeof(long long), cudaMemcpyDeviceToHost, st));
     JFNK_TRY(residual64(p, u, p.F64, p.Au64, st));
@@ -913,10 +925,12 @@ static jfnk_status solve_T(P& p, const jfnk_options& o, double* u, jfnk_stats* s
             const double f0 = 0.5 * normF * normF;
             double prev_a = -1.0, prev_f = 0.0;
             bool ok = false;
+            int trials = 0;
             for (int ls = 0; ls < o.ls_max; ++ls) {
                 JFNK_TRY(add_scaled(p.utrial, u, alpha, p.delta, N, st));
                 JFNK_TRY(residual64(p, p.utrial, p.Ftrial, p.Autrial, st));
                 JFNK_TRY(read_norm(p, p.Ftrial, &normT, st));
+                trials++;
                 const double fn = 0.5 * normT * normT;
                 if (std::isfinite(fn) && fn <= f0 + 1e-4 * alpha * slope) {
                     ok = true;
@@ -947,11 +961,22 @@ static jfnk_status solve_T(P& p, const jfnk_options& o, double* u, jfnk_stats* s
                 prev_f = fn;
                 alpha = t;
             }
-            if (!ok) result = JFNK_ERR_LINESEARCH;
+            if (k < JFNK_MAX_HIST) S.ls_hist[k] = trials;
+            if (!ok) {
+                // no sufficient decrease: the step is not taken and the solve
+                // stops at the last accepted iterate (Dennis & Schnabel, Sec. 6.3)
+                result = JFNK_ERR_LINESEARCH;
+                if (k + 1 < JFNK_MAX_HIST) S.res_hist[k + 1] = normF;
+                if (k < JFNK_MAX_HIST) S.alpha_hist[k] = 0.0;
+                set_error("line search found no sufficient decrease in %d trials at Newton step %d", trials, k);
+                k++;
+                break;
+            }
         } else {
             JFNK_TRY(add_scaled(p.utrial, u, 1.0, p.delta, N, st));
             JFNK_TRY(residual64(p, p.utrial, p.Ftrial, p.Autrial, st));
             JFNK_TRY(read_norm(p, p.Ftrial, &normT, st));
+            if (k < JFNK_MAX_HIST) S.ls_hist[k] = 1;
         }
         JFNK_CUDA_TRY(cudaMemcpyAsync(u, p.utrial, sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
         std::swap(p.F64, p.Ftrial);
@@ -959,11 +984,6 @@ static jfnk_status solve_T(P& p, const jfnk_options& o, double* u, jfnk_stats* s
         normF = normT;
         if (k + 1 < JFNK_MAX_HIST) S.res_hist[k + 1] = normF;
         if (k < JFNK_MAX_HIST) S.alpha_hist[k] = alpha;
-        if (result == JFNK_ERR_LINESEARCH) {
-            set_error("line search failed at Newton step %d", k);
-            k++;
-            break;
-        }
     }
     S.newton_its = k;
     S.converged = converged(normF) ? 1 : 0;
@@ -978,6 +998,7 @@ static jfnk_status solve_T(P& p, const jfnk_options& o, double* u, jfnk_stats* s
     double ge = 0.0;
     for (int l = 0; l <= p.L && l < JFNK_MAX_LEVELS; ++l) {
         S.nF[l] = p.nF[l];
+        S.nJv[l] = p.nF[l] - p.nFplain[l];
         ge += std::pow(2.0, -(double)p.d * (p.L - l)) * (double)p.nF[l];
         double lam = 0.0;
         if (l >= 1) {
@@ -1506,7 +1527,7 @@ static jfnk_status adjoint_T(P& p, const jfnk_options& o, const double* u, const
         explicit AdjGuard(P& qq) : q(qq) { q.adj = true; }
         ~AdjGuard() { q.adj = false; }
     } guard(p);
-    for (int l = 0; l <= p.L; ++l) p.nF[l] = 0;
+    for (int l = 0; l <= p.L; ++l) p.nF[l] = p.nFplain[l] = 0;
     const Grid& gf = p.lv[p.L].g;
     // hierarchy at u; the power method now estimates lambda of J^T (same spectrum as J)
     JFNK_TRY(mg_setup_T<T>(p, o, u, 0, st));
@@ -1535,6 +1556,7 @@ static jfnk_status adjoint_T(P& p, const jfnk_options& o, const double* u, const
         double ge = 0.0;
         for (int l = 0; l <= p.L && l < JFNK_MAX_LEVELS; ++l) {
             S.nF[l] = p.nF[l];
+            S.nJv[l] = p.nF[l] - p.nFplain[l];
             ge += std::pow(2.0, -(double)p.d * (p.L - l)) * (double)p.nF[l];
             if (l >= 1) JFNK_CUDA_TRY(cudaMemcpy(&S.lambda_max[l], p.lv[l].lam, sizeof(double), cudaMemcpyDeviceToHost));
         }

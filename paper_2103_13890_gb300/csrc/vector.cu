@@ -47,22 +47,97 @@ __global__ void masked_stat_kernel(Grid g, const T* x, int what, double* out, do
     }
 }
 
+// Scalar grids (nc = 1): the interior is (n-1)^(d-1) rows of n-1 contiguous
+// entries.  One warp per row, lanes along x, rows dealt to warps in a fixed
+// order (reproducible sums); one integer division per row instead of two per
+// entry.  FP32 vectors are summed in FP32 over at most 8 entries per lane and
+// row, then in FP64 (the FP64 pipe runs at 1/64 of the FP32 rate on this GPU,
+// so converting every entry to FP64 made these reductions ALU-bound).
+constexpr int kRowWarps = kVecThreads / 32;
+constexpr int kRowUnroll = 8;
+
+__host__ __device__ __forceinline__ long long interior_rows(const Grid& g) {
+    const long long m = g.n - 1;
+    return g.d == 3 ? m * m : m;
+}
+
+// Offset of the first entry (x = 0) of interior row r.
+__device__ __forceinline__ long long interior_row_base(const Grid& g, unsigned int r) {
+    const unsigned int m = (unsigned int)(g.n - 1);
+    if (g.d == 2) return (long long)(r + 1) * g.sy;
+    const unsigned int zz = r / m, yy = r - zz * m;
+    return (long long)(zz + 1) * g.sz + (long long)(yy + 1) * g.sy;
+}
+
 template <typename T>
-jfnk_status masked_stat(const Grid& g, const T* x, int what, double* out, RedScratch* red, cudaStream_t st) {
-    EpsParams ep{};
-    masked_stat_kernel<T><<<vec_blocks(g.size), kVecThreads, 0, st>>>(g, x, what, out, red->partial,
-                                                                      &red->counter[0], ep, nullptr, nullptr);
+__device__ __forceinline__ double row_stat(const T* __restrict__ row, int nx, int lane, int what) {
+    double acc = 0.0;
+    for (int x0 = 1 + lane; x0 < nx - 1; x0 += 32 * kRowUnroll) {
+        T f = T(0);
+#pragma unroll
+        for (int k = 0; k < kRowUnroll; ++k) {
+            const int x = x0 + 32 * k;
+            if (x < nx - 1) {
+                const T v = row[x];
+                f += (what == 0) ? (v < T(0) ? -v : v) : v * v;
+            }
+        }
+        acc += (double)f;
+    }
+    return acc;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kVecThreads) masked_stat_rows_kernel(Grid g, const T* __restrict__ x, int what,
+                                                                       double* out, double* partials,
+                                                                       unsigned int* counter, EpsParams ep,
+                                                                       EpsSlot* slot, double* norm_out) {
+    __shared__ double sm[32];
+    const int lane = threadIdx.x & 31;
+    const unsigned int nrows = (unsigned int)interior_rows(g);
+    const unsigned int wstride = gridDim.x * kRowWarps;
+    double acc = 0.0;
+    for (unsigned int r = blockIdx.x * kRowWarps + (threadIdx.x >> 5); r < nrows; r += wstride)
+        acc += row_stat<T>(x + interior_row_base(g, r), g.nx, lane, what);
+    double bs = block_sum(acc, sm);
+    double tot = 0.0;
+    if (grid_sum_last(bs, partials, counter, &tot, sm) && threadIdx.x == 0) {
+        double res = (what == 0) ? tot : sqrt(tot);
+        if (out) *out = res;
+        if (norm_out) *norm_out = res;
+        if (slot) set_eps_slot(slot, ep, res, ep.unit != 0, nullptr);
+    }
+}
+
+static int row_blocks(long long rows) {
+    long long b = (rows + kRowWarps - 1) / kRowWarps;
+    return (int)(b < kVecBlocks ? (b < 1 ? 1 : b) : kVecBlocks);
+}
+
+template <typename T>
+static jfnk_status launch_masked_stat(const Grid& g, const T* x, int what, double* out, const EpsParams& ep,
+                                      EpsSlot* slot, double* norm_out, RedScratch* red, cudaStream_t st) {
+    if (g.nc == 1 && !g.beam && g.n >= 2 && g.size <= 0x7fffffffLL) {
+        masked_stat_rows_kernel<T><<<row_blocks(interior_rows(g)), kVecThreads, 0, st>>>(
+            g, x, what, out, red->partial, &red->counter[0], ep, slot, norm_out);
+    } else {
+        masked_stat_kernel<T><<<vec_blocks(g.size), kVecThreads, 0, st>>>(g, x, what, out, red->partial,
+                                                                          &red->counter[0], ep, slot, norm_out);
+    }
     JFNK_LAUNCH_CHECK();
     return JFNK_OK;
 }
 
 template <typename T>
+jfnk_status masked_stat(const Grid& g, const T* x, int what, double* out, RedScratch* red, cudaStream_t st) {
+    EpsParams ep{};
+    return launch_masked_stat<T>(g, x, what, out, ep, nullptr, nullptr, red, st);
+}
+
+template <typename T>
 jfnk_status norm_to_eps(const Grid& g, const T* v, const EpsParams& ep, EpsSlot* slot, double* norm_out,
                         RedScratch* red, cudaStream_t st) {
-    masked_stat_kernel<T><<<vec_blocks(g.size), kVecThreads, 0, st>>>(g, v, 1, nullptr, red->partial,
-                                                                      &red->counter[0], ep, slot, norm_out);
-    JFNK_LAUNCH_CHECK();
-    return JFNK_OK;
+    return launch_masked_stat<T>(g, v, 1, nullptr, ep, slot, norm_out, red, st);
 }
 
 template jfnk_status masked_stat<float>(const Grid&, const float*, int, double*, RedScratch*, cudaStream_t);
@@ -395,11 +470,67 @@ __global__ void cheb_start_zero_kernel(Grid g, const T* __restrict__ b, T* __res
     }
 }
 
+// The same over the rows of a scalar grid (every row, so that the boundary
+// entries of r and d are written as zeros): one warp per row, the interior
+// test per row and per x, FP32 arithmetic for FP32 vectors (d = b / theta in
+// the vector's precision, the norm summed as in masked_stat_rows_kernel).
+template <typename T>
+__global__ void __launch_bounds__(kVecThreads) cheb_start_zero_rows_kernel(
+    Grid g, const T* __restrict__ b, T* __restrict__ r, T* __restrict__ d, const ChebTable* cheb, EpsParams ep,
+    EpsSlot* slot, double* partials, unsigned int* counter) {
+    __shared__ double sm[32];
+    const T ti = sizeof(T) == 4 ? (T)cheb->theta_invf : (T)cheb->theta_inv;
+    const int lane = threadIdx.x & 31;
+    const unsigned int nrows = (unsigned int)(g.ny * g.nz);
+    const unsigned int wstride = gridDim.x * kRowWarps;
+    const int nx = g.nx;
+    double acc = 0.0;
+    for (unsigned int row = blockIdx.x * kRowWarps + (threadIdx.x >> 5); row < nrows; row += wstride) {
+        const unsigned int zz = row / (unsigned int)g.ny, yy = row - zz * (unsigned int)g.ny;
+        const bool inner_row = yy > 0 && yy < (unsigned int)g.ny - 1 && (g.d == 2 || (zz > 0 && zz < (unsigned int)g.nz - 1));
+        const long long base = (long long)row * g.sy;
+        const T* br = b + base;
+        T* rr = r + base;
+        T* dr = d + base;
+        for (int x0 = lane; x0 < nx; x0 += 32 * kRowUnroll) {
+            T f = T(0);
+#pragma unroll
+            for (int k = 0; k < kRowUnroll; ++k) {
+                const int x = x0 + 32 * k;
+                if (x < nx) {
+                    const bool in = inner_row && x > 0 && x < nx - 1;
+                    const T bv = in ? br[x] : T(0);
+                    const T dv = bv * ti;
+                    rr[x] = bv;
+                    dr[x] = dv;
+                    f += dv * dv;
+                }
+            }
+            acc += (double)f;
+        }
+    }
+    double bs = block_sum(acc, sm);
+    double tot = 0.0;
+    if (grid_sum_last(bs, partials, counter, &tot, sm) && threadIdx.x == 0) {
+        double e = eps_formula(ep.mode, ep.n_unknowns, *ep.xstat, sqrt(tot));
+        double inv = e > 0.0 ? 1.0 / e : 0.0;
+        slot->e = e;
+        slot->inv = inv;
+        slot->ef = (float)e;
+        slot->invf = (float)inv;
+    }
+}
+
 template <typename T>
 jfnk_status cheb_start_zero(const Grid& g, const T* b, T* r, T* d, const ChebTable* cheb, const EpsParams& ep,
                             EpsSlot* slot, RedScratch* red, cudaStream_t st) {
-    cheb_start_zero_kernel<T><<<vec_blocks(g.size), kVecThreads, 0, st>>>(g, b, r, d, cheb, ep, slot, red->partial,
-                                                                          &red->counter[0]);
+    if (g.nc == 1 && !g.beam && g.n >= 2 && g.size <= 0x7fffffffLL) {
+        cheb_start_zero_rows_kernel<T><<<row_blocks((long long)g.ny * g.nz), kVecThreads, 0, st>>>(
+            g, b, r, d, cheb, ep, slot, red->partial, &red->counter[0]);
+    } else {
+        cheb_start_zero_kernel<T><<<vec_blocks(g.size), kVecThreads, 0, st>>>(g, b, r, d, cheb, ep, slot,
+                                                                              red->partial, &red->counter[0]);
+    }
     JFNK_LAUNCH_CHECK();
     return JFNK_OK;
 }

@@ -1,0 +1,86 @@
+"""Final-solution parity at the sizes of the configured workloads, element by
+element, against the oracle (final solution <= 1e-8 relative):
+
+  * 3D nonlinear diffusion, 65^3 and 129^3 nodes, V(2,2) Chebyshev degree 4,
+    FGMRES(30), 1e-8 -- the FP64 solve (the bench's configuration at 129^3)
+    and the FP32-preconditioned solve (FP64 Newton/FGMRES).  The oracle's
+    converged solutions at these sizes take minutes on a CPU core, so a
+    committed script (tests/golden/make_nd_solutions.py, oracle only) stored
+    4096 sampled nodal values and the norms of each; the GPU solution is
+    compared at those nodes and by its norms.
+  * the 64-instance batched Bratu workload (129^2 / 257^2 / 513^2 nodes,
+    lambda ~ U[1, 6.5], FP32 preconditioner): one instance of every size
+    against the oracle's exact-Newton solution (sparse direct solves), and
+    against its own single-problem solve.
+Both sides are converged far below the stopping rule's 1e-8 (the Newton steps
+converge quadratically), so 1e-8 leaves the discretisation's answer as the
+only thing compared."""
+import functools
+
+import numpy as np
+import pytest
+
+from golden import make_nd_solutions
+from gpu_common import host, jf, rel, torch
+from oracle import adjoint
+from workloads import batch_instances
+
+pytestmark = pytest.mark.gpu
+
+
+@functools.lru_cache(maxsize=None)
+def _gpu_nd(n, levels, pc):
+    m = jf()
+    o = m.default_options(nu_pre=2, nu_post=2, cheb_degree=4, rtol_newton=1e-8,
+                          pc_dtype=m.F32 if pc == "f32" else m.F64,
+                          eps_mode_pc=m.EPS_FP32 if pc == "f32" else m.EPS_PAPER)
+    p = m.Problem("nd3d", n, levels, options=o)
+    u = torch.zeros((n + 1,) * 3, dtype=torch.float64, device="cuda")
+    st = p.solve(u)
+    return host(u), st
+
+
+@pytest.mark.parametrize("n,levels", [(64, 5), (128, 6)])
+@pytest.mark.parametrize("pc", ["f64", "f32"])
+def test_nd_solution_matches_the_oracle_at_sampled_nodes(n, levels, pc):
+    idx, val, hdr = make_nd_solutions.load(n + 1)
+    u, st = _gpu_nd(n, levels, pc)
+    assert st["converged"]
+    got = u.ravel()[idx]
+    # element by element at the sampled nodes, relative to the solution's size
+    assert np.max(np.abs(got - val)) <= 1e-8 * hdr["normmax"]
+    assert rel(got, val) <= 1e-8
+    # and the whole vector through its norms
+    assert abs(np.linalg.norm(u) - hdr["norm2"]) <= 1e-8 * hdr["norm2"]
+    assert abs(u.sum() - hdr["sum"]) <= 1e-8 * abs(hdr["sum"])
+    assert abs(np.abs(u).max() - hdr["normmax"]) <= 1e-8 * hdr["normmax"]
+
+
+def _levels(n, coarse=8):
+    return int(np.log2(n // coarse)) + 1
+
+
+def test_batch_workload_instances_match_exact_newton():
+    inst = batch_instances(64, seed=4)
+    m = jf()
+    o = m.default_options(rtol_newton=1e-8, pc_dtype=m.F32, eps_mode_pc=m.EPS_FP32)
+    ps = [m.Problem("bratu2d", n, _levels(n), lam=lam, options=o) for n, lam in inst]
+    us = [torch.zeros((n + 1, n + 1), dtype=torch.float64, device="cuda") for n, _ in inst]
+    stats = m.solve_batched(ps, us, o)
+    assert all(s["converged"] for s in stats)
+    # one instance of each size: the one with the largest lambda (closest to
+    # the fold of the Bratu branch, the hardest solve)
+    pick = {}
+    for k, (n, lam) in enumerate(inst):
+        if n not in pick or lam > inst[pick[n]][1]:
+            pick[n] = k
+    assert sorted(pick) == [128, 256, 512]
+    for n, k in sorted(pick.items()):
+        lam = inst[k][1]
+        ub = host(us[k])
+        ud, _ = adjoint.newton_direct("bratu2d", np.zeros((n + 1, n + 1)), lam=lam)
+        assert rel(ub, ud) <= 1e-8, (n, lam)
+        q = m.Problem("bratu2d", n, _levels(n), lam=lam, options=o)
+        u1 = torch.zeros_like(us[k])
+        q.solve(u1)
+        assert rel(ub, host(u1)) <= 1e-8, (n, lam)
