@@ -172,23 +172,19 @@ def oracle_solve(n=ORACLE_N, levels=ORACLE_LEVELS):
 
 def oracle_baseline(reps=2):
     """cpu_baseline: the oracle's complete solve at 33^3 nodes, timed `reps`
-    times (best reported); the 129^3 figure beside it is an estimate that
-    scales by the unknowns (GE per solve is level-independent, Sec. 3)."""
+    times (best reported)."""
     ts = []
     for _ in range(reps):
         t, st = oracle_solve()
         ts.append(t)
     t = min(ts)
     unknowns = (ORACLE_N - 1) ** 3
-    est = t * (N_ELEM - 1) ** 3 / unknowns
     return {"value": t, "unit": "s", "cores": 1, "kind": "oracle", "threads": 1, **host_info(),
             "sample": (f"complete oracle JFNK-MG solve of the same problem at {ORACLE_N + 1}^3 nodes "
                        f"({unknowns} unknowns, {ORACLE_LEVELS} levels, same settings): {st.newton_its} Newton, "
                        f"{st.linear_its} FGMRES, GE {st.ge:.1f}; best of {reps}: "
                        + ", ".join(f"{x:.2f}" for x in ts) + " s"),
-            "workload": f"nd3d_{ORACLE_N + 1}^3_fp64_V(2,2)_cheb4_fgmres30_rtol1e-8",
-            "estimate_129_s": est,
-            "estimate_129_basis": "value x unknowns(129^3) / unknowns(33^3); an estimate, not a measurement"}
+            "workload": f"nd3d_{ORACLE_N + 1}^3_fp64_V(2,2)_cheb4_fgmres30_rtol1e-8"}
 
 
 def reference_arm(args):
@@ -219,8 +215,6 @@ def reference_arm(args):
         "cpu_baseline": {"value": val, "unit": "s", "cores": 1, "threads": 1, "kind": "oracle", "sample": sample,
                          **host_info()},
         "e2e": {"value": val, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
-        "estimate_129_s": val * (N_ELEM - 1) ** 3 / unknowns,
-        "estimate_129_basis": "value x unknowns(129^3) / unknowns(33^3); an estimate, not a measurement",
     }
     print(json.dumps(line), flush=True)
     return 0

@@ -311,9 +311,10 @@ jfnk_status jfnk_adjoint_solve(jfnk_problem* p, const jfnk_options* opts, const 
  * completion counters, the FD step; about 16 KB) is a file-scope __device__
  * array that every GPU which loads libjfnk.so holds until the process exits.
  * Sizes: 2 <= n_elem <= JFNK_NOALLOC_MAX_N3D (3D) or JFNK_NOALLOC_MAX_N2D (2D);
- * larger grids return JFNK_ERR_INVALID_ARG.  The first call on a device looks up
- * the scratch's device address (with that device current); make that first call
- * before any stream capture.  Every call clears the completion counters it needs
+ * larger grids return JFNK_ERR_INVALID_ARG.  Every call looks up the scratch's
+ * device address on the current device (cudaGetSymbolAddress); the first lookup
+ * on a device may load the library's device code there, so make the first call
+ * on each device before any stream capture.  Every call clears the completion counters it needs
  * on `stream` and otherwise reuses the previous call's scratch contents, so calls
  * that overlap on the GPU (other streams, other threads) race on the scratch:
  * serialise them. */
@@ -339,6 +340,16 @@ const char* jfnk_last_error(void);
  * 5-20 ms kernels on `stream` and synchronises it.  Allocates nothing. */
 jfnk_status jfnk_measure_peaks(double* fp64_fma_per_s, double* fp32_fma_per_s, double* fp32x2_fma_per_s,
                                void* stream);
+
+/* Bounds record of a bounds-checked build (compiled with -DJFNK_DEBUG_BOUNDS;
+ * the paper has no counterpart).  Such a build checks the computed indices of
+ * the element kernels, transfers and reductions before each access; an index
+ * out of range is clamped into range (no fault, no trap) and the source line
+ * of the first one is recorded in device memory.  *enabled = 1 in such a build,
+ * 0 otherwise; *line = the first recorded line (0: none; the file is in
+ * jfnk_last_error()); reset = 1 clears the record.  Host pointers; reads device
+ * memory synchronously. */
+jfnk_status jfnk_debug_bounds(int* enabled, unsigned int* line, int reset);
 
 /* Number of kernels this library launched on the calling thread since the last
  * reset (returns the count; reset = 1 then clears it).  A replayed V-cycle

@@ -334,6 +334,14 @@ def measure_peaks():
     return {"fp64": a.value, "fp32": b.value, "fp32x2": c.value}
 
 
+def debug_bounds(reset=True):
+    """(enabled, first out-of-range source line or 0, message) of a bounds-checked
+    build (jfnk_debug_bounds); enabled is False in a normal build."""
+    en, line = ctypes.c_int(), ctypes.c_uint()
+    _check(lib().jfnk_debug_bounds(ctypes.byref(en), ctypes.byref(line), 1 if reset else 0))
+    return bool(en.value), line.value, last_error() if line.value else ""
+
+
 def kernel_launches(reset=False):
     """Kernels the library has launched (graph replays count their kernels);
     reset=True returns the count and restarts it."""

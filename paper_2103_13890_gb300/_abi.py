@@ -3,7 +3,8 @@ import ctypes
 import os
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "lib", "libjfnk.so")
+# JFNK_LIB selects another build of the library (e.g. the bounds-checked one)
+LIB_PATH = os.environ.get("JFNK_LIB") or os.path.join(HERE, "lib", "libjfnk.so")
 
 MAX_LEVELS = 16
 MAX_HIST = 64
@@ -77,6 +78,7 @@ SIGNATURES = [
     ("jfnk_set_kappa", _i, [_vp, _vp, _vp]),
     ("jfnk_adjoint_solve", _i, [_vp, ctypes.POINTER(Options), _vp, _vp, _vp, _vp, _d, ctypes.POINTER(Stats), _vp]),
     ("jfnk_measure_peaks", _i, [ctypes.POINTER(_d), ctypes.POINTER(_d), ctypes.POINTER(_d), _vp]),
+    ("jfnk_debug_bounds", _i, [ctypes.POINTER(_i), ctypes.POINTER(ctypes.c_uint), _i]),
     ("jfnk_profile_enable", None, [_i]),
     ("jfnk_profile_read", _i, [_i, ctypes.c_char_p, _i, ctypes.POINTER(ctypes.c_longlong),
                                ctypes.POINTER(_d), ctypes.POINTER(_d)]),

@@ -110,6 +110,40 @@ __host__ __device__ __forceinline__ bool grid_unknown(const Grid& g, long long i
 void set_error(const char* fmt, ...);
 void count_launch(int k = 1);
 
+// Bounds-checked builds (compiled with -DJFNK_DEBUG_BOUNDS): JFNK_IDX(i, n)
+// checks 0 <= i < n before an access.  An index out of range is recorded (the
+// source line of the first one, in a device word of its translation unit) and
+// clamped into range, so the kernel neither faults nor traps and the host
+// reads the record afterwards (jfnk_debug_bounds).  In normal builds the
+// macro is the index itself.
+typedef unsigned int (*BoundsReader)(int reset);
+int register_bounds_reader(BoundsReader reader, const char* file);
+#ifdef JFNK_DEBUG_BOUNDS
+static __device__ unsigned int g_bounds_line;  // one per translation unit
+#ifdef __CUDACC__
+__device__ __forceinline__ long long dbg_idx(long long i, long long n, unsigned int line) {
+    if (i < 0 || i >= n) {
+        atomicCAS(&g_bounds_line, 0u, line);
+        return i < 0 ? 0 : (n > 0 ? n - 1 : 0);
+    }
+    return i;
+}
+#endif
+static unsigned int read_bounds_line(int reset) {
+    unsigned int v = 0;
+    if (cudaMemcpyFromSymbol(&v, g_bounds_line, sizeof(v)) != cudaSuccess) return 0xffffffffu;
+    if (reset) {
+        const unsigned int z = 0;
+        cudaMemcpyToSymbol(g_bounds_line, &z, sizeof(z));
+    }
+    return v;
+}
+static const int g_bounds_registered = register_bounds_reader(&read_bounds_line, __FILE__);
+#define JFNK_IDX(i, n) ::jfnk::dbg_idx((long long)(i), (long long)(n), __LINE__)
+#else
+#define JFNK_IDX(i, n) (i)
+#endif
+
 #define JFNK_CUDA_TRY(expr)                                                          \
     do {                                                                             \
         cudaError_t e_ = (expr);                                                     \

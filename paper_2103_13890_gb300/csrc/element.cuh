@@ -63,18 +63,20 @@ __host__ __device__ __forceinline__ void h2_adj(const T F[2][2], T& w00, T& w10,
 //         i.e. the element residual divided by 3h/16, which the caller applies
 //         once per node.
 // ---------------------------------------------------------------------------
+// Middle of the element for its modal inputs: a_pq and b_pq are the x/y
+// butterflies of the nodal values on the element's lower (c = 0) and upper
+// (c = 1) z face (p: x mode, q: y mode; mode 0 = sum, mode 1 = difference), and
+// the outputs are the test-function modes R_pqr (R_000 = 0) before the
+// transposed butterflies.  elem_nd3 below is forward butterflies + this +
+// transposed butterflies; the z-marching kernels share the face butterflies of
+// neighbouring elements and call this directly (same operations, same order).
 template <typename T, bool KAPPA>
-__host__ __device__ __forceinline__ void elem_nd3(const T u[8], T kap, T r[8]) {
+__host__ __device__ __forceinline__ void elem_nd3_mid(T a00, T a01, T a10, T a11, T b00, T b01, T b10, T b11,
+                                                      T kap, T& R001, T& R010, T& R011, T& R100, T& R101,
+                                                      T& R110, T& R111) {
     const T A1 = T(0.57735026918962576451);   // 1/sqrt(3)
     const T A2 = T(0.33333333333333333333);   // 1/3
     const T A3 = T(0.19245008972987525484);   // 1/(3 sqrt 3)
-    // modal transform M' = T' (x) T' (x) T' u, T' = [[1,1],[-1,1]]  (24 ops)
-    T p0 = u[0] + u[1], q0 = u[1] - u[0];
-    T p1 = u[2] + u[3], q1 = u[3] - u[2];
-    T p2 = u[4] + u[5], q2 = u[5] - u[4];
-    T p3 = u[6] + u[7], q3 = u[7] - u[6];
-    T a00 = p0 + p1, a01 = p1 - p0, b00 = p2 + p3, b01 = p3 - p2;  // x-mode 0
-    T a10 = q0 + q1, a11 = q1 - q0, b10 = q2 + q3, b11 = q3 - q2;  // x-mode 1
     // S_pqr = M'_pqr A^(p+q+r) / 8  (8 ops)
     // (A^k / 8 is exact in either precision: the scaling by 2^-3 does not round)
     const T A1s = T(0.57735026918962576451 * 0.125), A2s = T(0.33333333333333333333 * 0.125),
@@ -124,11 +126,26 @@ __host__ __device__ __forceinline__ void elem_nd3(const T u[8], T kap, T r[8]) {
     h2_adj(FY, Y00, Y10, Y01, Y11);  // Y_pr
     h2_adj(FZ, Z00, Z10, Z01, Z11);  // Z_pq
     // test-function modes, scaled by A^(p+q+r) (12 ops)
-    T R100 = X00 * A1, R010 = Y00 * A1, R001 = Z00 * A1;
-    T R110 = (X10 + Y10) * A2;
-    T R101 = (X01 + Z10) * A2;
-    T R011 = (Y01 + Z01) * A2;
-    T R111 = (X11 + Y11 + Z11) * A3;
+    R100 = X00 * A1;
+    R010 = Y00 * A1;
+    R001 = Z00 * A1;
+    R110 = (X10 + Y10) * A2;
+    R101 = (X01 + Z10) * A2;
+    R011 = (Y01 + Z01) * A2;
+    R111 = (X11 + Y11 + Z11) * A3;
+}
+
+template <typename T, bool KAPPA>
+__host__ __device__ __forceinline__ void elem_nd3(const T u[8], T kap, T r[8]) {
+    // modal transform M' = T' (x) T' (x) T' u, T' = [[1,1],[-1,1]]  (24 ops)
+    T p0 = u[0] + u[1], q0 = u[1] - u[0];
+    T p1 = u[2] + u[3], q1 = u[3] - u[2];
+    T p2 = u[4] + u[5], q2 = u[5] - u[4];
+    T p3 = u[6] + u[7], q3 = u[7] - u[6];
+    T a00 = p0 + p1, a01 = p1 - p0, b00 = p2 + p3, b01 = p3 - p2;  // x-mode 0
+    T a10 = q0 + q1, a11 = q1 - q0, b10 = q2 + q3, b11 = q3 - q2;  // x-mode 1
+    T R001, R010, R011, R100, R101, R110, R111;
+    elem_nd3_mid<T, KAPPA>(a00, a01, a10, a11, b00, b01, b10, b11, kap, R001, R010, R011, R100, R101, R110, R111);
     // transpose of the modal transform (R000 = 0)  (24 ops)
     // z pass: (mode r) -> (c)
     T e00_0 = -R001, e00_1 = R001;            // (p,q) = (0,0)

@@ -11,7 +11,6 @@
 // that loads the library and which stays allocated there until the process
 // exits.
 #include <cstring>
-#include <mutex>
 
 #include "common.cuh"
 #include "stencil.cuh"
@@ -36,30 +35,17 @@ constexpr size_t kNoAllocScratchBytes = (sizeof(NoAllocScratch) + 255) / 256 * 2
 // cudaGetSymbolAddress: its device address is looked up per device below.
 static __device__ __align__(256) unsigned char g_jvp_noalloc_scratch[kNoAllocScratchBytes];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_mutex;
-void* g_scratch_addr[kMaxDevices] = {};
-
-// Device address of the scratch on the current device; looked up once per
-// device (the first call on a device, with that device current).
+// Device address of the scratch on the current device, looked up on every call
+// (cudaGetSymbolAddress is a cheap host-side query), so that no address cached
+// from an earlier context can outlive a device reset.
 jfnk_status scratch_on_current_device(NoAllocScratch** out) {
-    int dev = -1;
-    JFNK_CUDA_TRY(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= kMaxDevices) {
-        set_error("device %d out of range for the no-alloc scratch table", dev);
-        return JFNK_ERR_INVALID_ARG;
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_jvp_noalloc_scratch);
+    if (e != cudaSuccess || !p) {
+        set_error("cudaGetSymbolAddress of the no-alloc scratch failed: %s", cudaGetErrorString(e));
+        return JFNK_ERR_CUDA;
     }
-    std::lock_guard<std::mutex> lock(g_mutex);
-    if (!g_scratch_addr[dev]) {
-        void* p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_jvp_noalloc_scratch);
-        if (e != cudaSuccess || !p) {
-            set_error("cudaGetSymbolAddress of the no-alloc scratch failed: %s", cudaGetErrorString(e));
-            return JFNK_ERR_CUDA;
-        }
-        g_scratch_addr[dev] = p;
-    }
-    *out = reinterpret_cast<NoAllocScratch*>(g_scratch_addr[dev]);
+    *out = reinterpret_cast<NoAllocScratch*>(p);
     return JFNK_OK;
 }
 

@@ -24,6 +24,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "coarse.cuh"
 #include "common.cuh"
 #include "stencil.cuh"
@@ -51,6 +53,22 @@ void set_error(const char* fmt, ...) {
     g_err = buf;
 }
 void count_launch(int k) { g_launches += k; }
+
+namespace {
+struct BoundsEntry {
+    BoundsReader reader;
+    const char* file;
+};
+std::vector<BoundsEntry>& bounds_registry() {
+    static std::vector<BoundsEntry> r;
+    return r;
+}
+}  // namespace
+
+int register_bounds_reader(BoundsReader reader, const char* file) {
+    bounds_registry().push_back({reader, file});
+    return (int)bounds_registry().size();
+}
 
 struct Level {
     Grid g;
@@ -113,6 +131,12 @@ struct jfnk_problem {
     // 3D levels with n <= ep_max_n run the element-parallel kernels (per precision)
     int ep_max_n64 = 1 << 20;
     int ep_max_n32 = 64;
+    // element-parallel levels with n >= this march element columns along z
+    // (0: never), per precision.  FP64: off -- the column kernel does ~10 %
+    // fewer FP64 operations but ran 5-20 % slower than one element a thread at
+    // n = 64..256 (fewer warps to keep the FP64 pipe fed)
+    int zm_min_n64 = 0;
+    int zm_min_n32 = 0;
     // CTA-size cap of the halo-free 3D kernel (per precision)
     int v2_threads64 = 1024;
     int v2_threads32 = 1024;
@@ -134,6 +158,22 @@ struct jfnk_problem {
 namespace jfnk {
 
 using P = jfnk_problem;
+
+// NVTX range over a host-side phase (a level operation of the V-cycle, the
+// set-up, a Krylov iteration, the line search), so that a timeline profiler
+// shows the method's structure.  Without an attached profiler the calls are
+// no-ops.  Ranges opened while a V-cycle is captured into a CUDA graph mark the
+// capture only; graph replays carry no ranges.
+struct Range {
+    explicit Range(const char* fmt, int a = 0, int b = 0) {
+        char buf[64];
+        snprintf(buf, sizeof(buf), fmt, a, b);
+        nvtxRangePushA(buf);
+    }
+    ~Range() { nvtxRangePop(); }
+    Range(const Range&) = delete;
+    Range& operator=(const Range&) = delete;
+};
 
 static inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
@@ -186,6 +226,8 @@ static size_t plan(P& p, char* base, const jfnk_options* o) {
     const size_t N = (size_t)gf.size;
     if (const char* e = getenv("JFNK_EP3D_MAX_N_F64")) p.ep_max_n64 = atoi(e);
     if (const char* e = getenv("JFNK_EP3D_MAX_N_F32")) p.ep_max_n32 = atoi(e);
+    if (const char* e = getenv("JFNK_ZM3D_MIN_N_F64")) p.zm_min_n64 = atoi(e);
+    if (const char* e = getenv("JFNK_ZM3D_MIN_N_F32")) p.zm_min_n32 = atoi(e);
     if (const char* e = getenv("JFNK_V2_THREADS_F64")) p.v2_threads64 = atoi(e);
     if (const char* e = getenv("JFNK_V2_THREADS_F32")) p.v2_threads32 = atoi(e);
     if (const char* e = getenv("JFNK_V3_F32")) p.v3_f32 = atoi(e);
@@ -313,6 +355,7 @@ static StencilArgs<T> base_args(P& p, int l) {
     a.face = reinterpret_cast<T*>(p.face);
     a.face_cap = (long long)(p.face_bytes / sizeof(T));
     a.ep_max_n = sizeof(T) == 8 ? p.ep_max_n64 : p.ep_max_n32;
+    a.zm_min_n = sizeof(T) == 8 ? p.zm_min_n64 : p.zm_min_n32;
     a.v2_threads = sizeof(T) == 8 ? p.v2_threads64 : p.v2_threads32;
     a.v3 = sizeof(T) == 4 ? p.v3_f32 : 0;
     return a;
@@ -340,6 +383,7 @@ static jfnk_status smooth(P& p, const jfnk_options& o, int l, const T* b, T* s, 
     Level& L = p.lv[l];
     const int k = o.cheb_degree;
     const EpsParams ep = eps_params(p, l, o.eps_mode_pc);
+    Range rg("smooth l%d nu%d", l, nu);
     for (int app = 0; app < nu; ++app) {
         T* dc = as<T>(L.d0);
         T* dn = as<T>(L.d1);
@@ -398,6 +442,7 @@ static jfnk_status smooth(P& p, const jfnk_options& o, int l, const T* b, T* s, 
 
 template <typename T>
 static jfnk_status coarse_solve(P& p, const jfnk_options& o, const T* b, T* s, cudaStream_t st) {
+    Range rg("coarse solve");
     Level& L = p.lv[0];
     CoarseArgs<T> a;
     memset(&a, 0, sizeof(a));
@@ -441,6 +486,7 @@ static jfnk_status vcycle(P& p, const jfnk_options& o, int l, T* b, T* s, cudaSt
     // r_(l-1) = R (b - J s)        (Alg. 1, restriction of the residual)
     if (o.nu_pre == 0) JFNK_TRY(set_eps(L.eps_s, 0.0, st));
     {
+        Range rg("restrict l%d", l);
         StencilArgs<T> a = base_args<T>(p, l);
         a.u = as<T>(L.x);
         a.v = s;
@@ -450,13 +496,16 @@ static jfnk_status vcycle(P& p, const jfnk_options& o, int l, T* b, T* s, cudaSt
         a.out = as<T>(L.t);
         JFNK_TRY(launch_op<T>(p, Mode::BMJ, a, st));
         p.nF[l]++;
+        JFNK_TRY(restrict_to<T>(L.g, C.g, as<T>(L.t), as<T>(C.b), false, st));
     }
-    JFNK_TRY(restrict_to<T>(L.g, C.g, as<T>(L.t), as<T>(C.b), false, st));
     // c_(l-1) = MG(x_(l-1), F(x_(l-1)), r_(l-1), l-1)
     JFNK_TRY(vcycle<T>(p, o, l - 1, as<T>(C.b), as<T>(C.s), st));
     // s += I c
-    JFNK_TRY(prolong_add<T>(C.g, L.g, as<T>(C.s), s, st));
-    JFNK_TRY(norm_to_eps<T>(L.g, s, eps_params(p, l, o.eps_mode_pc), L.eps_s, nullptr, p.red, st));
+    {
+        Range rg("prolong l%d", l);
+        JFNK_TRY(prolong_add<T>(C.g, L.g, as<T>(C.s), s, st));
+        JFNK_TRY(norm_to_eps<T>(L.g, s, eps_params(p, l, o.eps_mode_pc), L.eps_s, nullptr, p.red, st));
+    }
     JFNK_TRY(smooth<T>(p, o, l, b, s, o.nu_post, false, st));
     return JFNK_OK;
 }
@@ -509,6 +558,7 @@ static jfnk_status vcycle_graph(P& p, const jfnk_options& o, cudaStream_t st) {
 // x_L = u, x_(l-1) = P x_l, A(x_l), statistics for eps, power method (Sec. 2)
 template <typename T>
 static jfnk_status mg_setup_T(P& p, const jfnk_options& o, const double* u, int newton_step, cudaStream_t st) {
+    Range rg("mg setup (Newton step %d)", newton_step);
     Level& Lf = p.lv[p.L];
     if (newton_step == 0 && p.lb) {
         // the L-BFGS preconditioner of the coarse CG is built during the first
@@ -699,6 +749,7 @@ static jfnk_status fgmres(P& p, const jfnk_options& o, const double* u, double e
         double res = beta;
         bool stop = false;
         for (int j = 0; j < m; ++j) {
+            Range rg("FGMRES iteration %d", its);
             double* vj = p.V64 + (size_t)j * N;
             T* zj = Z + (size_t)j * N;
             // z_j = MG(v_j)
@@ -916,6 +967,7 @@ static jfnk_status solve_T(P& p, const jfnk_options& o, double* u, jfnk_stats* s
         if (k < JFNK_MAX_HIST) S.lin_hist[k] = its;
         // line search on phi(alpha) = 1/2 ||F(u + alpha delta)||^2
         double alpha = 1.0, normT = 0.0;
+        Range rg_ls("line search (Newton step %d)", k);
         if (o.line_search) {
             JFNK_TRY(jv64(p, u, p.Au64, p.delta, p.w64, st));
             JFNK_TRY(multi_dot(p.F64, p.w64, N, N, 1, p.hbuf, p.dot_partials, &p.counters[2], st));
@@ -1064,6 +1116,29 @@ using namespace jfnk;
 // definitions keep C linkage.
 
 const char* jfnk_last_error(void) { return g_err.c_str(); }
+
+jfnk_status jfnk_debug_bounds(int* enabled, unsigned int* line, int reset) {
+    using namespace jfnk;
+    int on = 0;
+#ifdef JFNK_DEBUG_BOUNDS
+    on = 1;
+#endif
+    if (enabled) *enabled = on;
+    unsigned int first = 0;
+    for (const auto& e : bounds_registry()) {
+        const unsigned int v = e.reader(reset);
+        if (v == 0xffffffffu) {
+            set_error("jfnk_debug_bounds: reading the record of %s failed", e.file);
+            return JFNK_ERR_CUDA;
+        }
+        if (v && !first) {
+            first = v;
+            set_error("index out of range at %s:%u", e.file, v);
+        }
+    }
+    if (line) *line = first;
+    return JFNK_OK;
+}
 
 long long jfnk_kernel_launches(int reset) {
     long long v = g_launches;

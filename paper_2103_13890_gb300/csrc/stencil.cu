@@ -63,7 +63,7 @@ __global__ void __launch_bounds__(K3_BX* K3_BY) stencil3d_kernel(const StencilAr
             const int x = x0 - 1 + lx, y = y0 - 1 + ly;
             T val = T(0);
             if (x >= 0 && x < g.nx && y >= 0 && y < g.ny && z >= 0 && z < g.nz) {
-                const long long idx = (long long)z * g.sz + (long long)y * g.sy + x;
+                const long long idx = JFNK_IDX((long long)z * g.sz + (long long)y * g.sy + x, g.size);
                 val = a.u[idx];
                 if (M != Mode::F) {
                     const bool bnd = x == 0 || x == g.nx - 1 || y == 0 || y == g.ny - 1 || z == 0 || z == g.nz - 1;
@@ -86,7 +86,7 @@ __global__ void __launch_bounds__(K3_BX* K3_BY) stencil3d_kernel(const StencilAr
             T ue[8] = {W[b0][ty][tx],     W[b0][ty][tx + 1],     W[b0][ty + 1][tx],     W[b0][ty + 1][tx + 1],
                        W[b1][ty][tx],     W[b1][ty][tx + 1],     W[b1][ty + 1][tx],     W[b1][ty + 1][tx + 1]};
             if (P == Prob::NDK3)
-                elem_nd3<T, true>(ue, a.kappa[((long long)k * n + ey) * n + ex], r);
+                elem_nd3<T, true>(ue, a.kappa[JFNK_IDX(((long long)k * n + ey) * n + ex, (long long)n * n * n)], r);
             else
                 elem_nd3<T, false>(ue, T(1), r);
         } else {

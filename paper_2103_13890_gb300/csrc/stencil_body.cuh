@@ -42,6 +42,7 @@ __device__ __forceinline__ ChebK<float> cheb_of<float>(const ChebTable* t, int i
 template <typename T, Mode M>
 __device__ __forceinline__ void epilogue(const StencilArgs<T>& a, long long idx, bool inner, T val,
                                          T inv_eps, const ChebK<T>& ck, float& red) {
+    idx = JFNK_IDX(idx, a.g.size);
     if (M == Mode::F) {
         T f = T(0), av = T(0);
         if (inner) {
@@ -108,6 +109,7 @@ __device__ __forceinline__ void epilogue(const StencilArgs<T>& a, long long idx,
 template <typename T, Mode M>
 __device__ __forceinline__ void epilogue_adj(const StencilArgs<T>& a, long long idx, bool inner, T jd,
                                              const ChebK<T>& ck, float& red) {
+    idx = JFNK_IDX(idx, a.g.size);
     if (M == Mode::JV) {
         const T o = inner ? jd : T(0);
         a.out[idx] = o;
@@ -207,7 +209,7 @@ __device__ __forceinline__ void stencil2d_body(const StencilArgs<T>& a, int x0, 
             const int x = x0 - 1 + i;
             T val = T(0);
             if (x >= 0 && x < g.nx && y >= 0 && y < g.ny) {
-                const long long idx = (long long)y * g.sy + x;
+                const long long idx = JFNK_IDX((long long)y * g.sy + x, g.size);
                 val = a.u[idx];
                 if (M != Mode::F) {
                     const bool bnd = x == 0 || x == g.nx - 1 || y == 0 || y == g.ny - 1;

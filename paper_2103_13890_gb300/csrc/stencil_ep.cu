@@ -47,7 +47,7 @@ __global__ void __launch_bounds__(kEpElemThreads) ep3d_elem_kernel(const Stencil
     const bool yz_in0 = y > 0, yz_in1 = y + 1 < n, z_in0 = z > 0, z_in1 = z + 1 < n;
     // node value (w, or u with the masked direction in vv for the adjoint) at (X, y+dy, z+dz)
     auto corner = [&](int X, int dy, int dz, T& wv, T& vv) {
-        const int idx = (z + dz) * sz + (y + dy) * sy + X;
+        const int idx = (int)JFNK_IDX((z + dz) * sz + (y + dy) * sy + X, a.g.size);
         const bool bnd = X == 0 || X == n || (dy ? !yz_in1 : !yz_in0) || (dz ? !z_in1 : !z_in0);
         T uv = a.u[idx];
         vv = T(0);
@@ -87,7 +87,7 @@ __global__ void __launch_bounds__(kEpElemThreads) ep3d_elem_kernel(const Stencil
     } else {
         elem_nd3<T, false>(ue, T(1), r);
     }
-    T* C = a.face + e;
+    T* C = a.face + JFNK_IDX(e, ne);
 #pragma unroll
     for (int c = 0; c < 8; ++c) C[c * ne] = r[c];
 }
@@ -117,7 +117,7 @@ __global__ void __launch_bounds__(kEpNodeThreads) ep3d_node_kernel(const Stencil
         T val = T(0);
         if (inner) {
             // element with corner c = dx + 2 dy + 4 dz at this node: (X-dx, Y-dy, Z-dz)
-            const T* Cn = C + (Z * esz + Y * esy + X);
+            const T* Cn = C + JFNK_IDX(Z * esz + Y * esy + X - esz - esy - 1, ne - esz - esy - 1) + esz + esy + 1;
             const T c0 = Cn[0], c1 = Cn[ne - 1];
             const T c2 = Cn[2 * ne - esy], c3 = Cn[3 * ne - esy - 1];
             const T c4 = Cn[4 * ne - esz], c5 = Cn[5 * ne - esz - 1];
@@ -128,6 +128,169 @@ __global__ void __launch_bounds__(kEpNodeThreads) ep3d_node_kernel(const Stencil
             epilogue_adj<T, M>(a, idx, inner, val, ck, red);
         else
             epilogue<T, M>(a, idx, inner, val, inv_eps, ck, red);
+    }
+    stencil_reduce(a, red, red_sm);
+}
+
+// ---------------------------------------------------------------------------
+// z-marching element columns (large FP64 levels).  Thread (x, y) evaluates the
+// elements (x, y, z) for z in its chunk, in order.  Neighbouring elements of a
+// column share a z face: the x/y butterflies of the face's nodal values
+// (elem_nd3_mid's a/b inputs) are computed once per face instead of once per
+// element, and on the test-function side the two elements' face modes are
+// summed before the y and x passes, so each face's 4 node sums leave the
+// thread already added over z.  The column's 4 per-plane node values go to
+// scratch Cz[k][z][y][x] (k = a + 2b: node (x+a, y+b, z)); the node kernel
+// adds the 4 columns around each node.  Against one element per thread this
+// saves 19 of ~183 FP64 operations per node (forward face butterflies, half
+// the nodal w = x + eps v, the y/x passes of one face, 4 of the 7 node adds)
+// and half of the scratch traffic.  A chunk that starts at z0 > 0 evaluates
+// element z0 - 1 once more (only its upper face modes are kept), so every
+// interior plane is completed inside one chunk and written once.
+// ---------------------------------------------------------------------------
+constexpr int kZmThreads = 128;
+
+__host__ __device__ inline long long zm3d_plane_stride(int n) { return (long long)(n + 1) * n * n; }
+
+template <typename T, Prob P, Mode M>
+__global__ void __launch_bounds__(kZmThreads) zm3d_elem_kernel(const StencilArgs<T> a, int zchunk) {
+    const int n = a.g.n;
+    const int sy = (int)a.g.sy, sz = (int)a.g.sz;
+    const int y = blockIdx.y;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    const bool valid = x < n;
+    const int xl = valid ? x : n - 1;  // inactive lanes still take part in the shuffles
+    const int z0 = blockIdx.z * zchunk;
+    const int z1 = min(n, z0 + zchunk);
+    const int zs = z0 > 0 ? z0 - 1 : 0;
+    T eps = T(0);
+    if (M != Mode::F) eps = eps_of<T>(a.eps);
+    const bool y_in0 = y > 0, y_in1 = y + 1 < n;
+    const bool own_right = (lane == 31) || (xl == n - 1);
+    // raw u (and v) of node (X, y + dy, Z); w = u + eps v formed by `wval`
+    auto load = [&](int X, int dy, int Z, T& uv, T& vv) {
+        const int idx = (int)JFNK_IDX(Z * sz + (y + dy) * sy + X, a.g.size);
+        uv = a.u[idx];
+        vv = T(0);
+        if (M != Mode::F) {
+            const bool bnd = X == 0 || X == n || (dy ? !y_in1 : !y_in0) || Z == 0 || Z == n;
+            if (!bnd) vv = a.v[idx];
+        }
+    };
+    // this thread's loads of plane Z: left nodes of rows y, y+1, and the right
+    // ones where no neighbour lane holds them
+    struct Raw {
+        T u0, v0, u1, v1, ur0, vr0, ur1, vr1;
+    };
+    auto fetch = [&](int Z, Raw& r) {
+        load(xl, 0, Z, r.u0, r.v0);
+        load(xl, 1, Z, r.u1, r.v1);
+        if (own_right) {
+            load(xl + 1, 0, Z, r.ur0, r.vr0);
+            load(xl + 1, 1, Z, r.ur1, r.vr1);
+        }
+    };
+    // face butterflies of a plane: s0 = p_0 + p_1, s1 = p_1 - p_0, s2 = q_0 + q_1,
+    // s3 = q_1 - q_0 with p_b / q_b the x sum / difference of row y + b
+    auto face = [&](const Raw& r, T& s0, T& s1, T& s2, T& s3) {
+        T l0 = r.u0, l1 = r.u1;
+        if (M != Mode::F) {
+            l0 = l0 + eps * r.v0;
+            l1 = l1 + eps * r.v1;
+        }
+        T r0 = __shfl_down_sync(0xffffffffu, l0, 1);
+        T r1 = __shfl_down_sync(0xffffffffu, l1, 1);
+        if (own_right) {
+            r0 = r.ur0;
+            r1 = r.ur1;
+            if (M != Mode::F) {
+                r0 = r0 + eps * r.vr0;
+                r1 = r1 + eps * r.vr1;
+            }
+        }
+        const T p0 = l0 + r0, q0 = r0 - l0;
+        const T p1 = l1 + r1, q1 = r1 - l1;
+        s0 = p0 + p1;
+        s1 = p1 - p0;
+        s2 = q0 + q1;
+        s3 = q1 - q0;
+    };
+    const long long ks = zm3d_plane_stride(n);
+    T* Cz = a.face;
+    const int col = y * n + x;
+    Raw cur;
+    fetch(zs, cur);
+    T a00, a01, a10, a11;
+    face(cur, a00, a01, a10, a11);
+    fetch(zs + 1, cur);
+    Raw nxt = cur;
+    T k00 = T(0), k01 = T(0), k10 = T(0), k11 = T(0);  // upper-face modes of the element below
+    T kap = T(1), kap_n = T(1);
+    if (P == Prob::NDK3 && valid) kap = a.kappa[JFNK_IDX((zs * n + y) * n + x, (long long)n * n * n)];
+    for (int z = zs; z < z1; ++z) {
+        // prefetch the plane above the next element
+        if (z + 2 <= n) fetch(z + 2, nxt);
+        if (P == Prob::NDK3 && valid && z + 1 < z1) kap_n = a.kappa[JFNK_IDX(((z + 1) * n + y) * n + x, (long long)n * n * n)];
+        T b00, b01, b10, b11;
+        face(cur, b00, b01, b10, b11);
+        T R001, R010, R011, R100, R101, R110, R111;
+        elem_nd3_mid<T, P == Prob::NDK3>(a00, a01, a10, a11, b00, b01, b10, b11, kap, R001, R010, R011, R100,
+                                         R101, R110, R111);
+        // z pass: lower-face (c = 0) and upper-face (c = 1) modes
+        const T e01_0 = R010 - R011, e01_1 = R010 + R011;
+        const T e10_0 = R100 - R101, e10_1 = R100 + R101;
+        const T e11_0 = R110 - R111, e11_1 = R110 + R111;
+        if (valid && z >= z0 && z >= 1) {
+            // plane z: this element's lower face plus the element below's upper face
+            const T E00 = k00 - R001, E01 = k01 + e01_0, E10 = k10 + e10_0, E11 = k11 + e11_0;
+            const T f0_0 = E00 - E01, f0_1 = E00 + E01;  // y pass, p = 0, b = 0 / 1
+            const T f1_0 = E10 - E11, f1_1 = E10 + E11;  // p = 1
+            T* Cp = Cz + JFNK_IDX((long long)z * n * n + col, ks);
+            Cp[0] = f0_0 - f1_0;       // node (x,   y,   z)
+            Cp[ks] = f0_0 + f1_0;      // node (x+1, y,   z)
+            Cp[2 * ks] = f0_1 - f1_1;  // node (x,   y+1, z)
+            Cp[3 * ks] = f0_1 + f1_1;  // node (x+1, y+1, z)
+        }
+        k00 = R001;
+        k01 = e01_1;
+        k10 = e10_1;
+        k11 = e11_1;
+        a00 = b00;
+        a01 = b01;
+        a10 = b10;
+        a11 = b11;
+        cur = nxt;
+        kap = kap_n;
+    }
+}
+
+// Node phase of the z-marching kernel: the 4 columns around node (X, Y, Z),
+// in a fixed order, then the epilogue of the mode and the norm reduction.
+template <typename T, Mode M>
+__global__ void __launch_bounds__(kEpNodeThreads) zm3d_node_kernel(const StencilArgs<T> a) {
+    __shared__ double red_sm[32];
+    const int n = a.g.n, NP = n + 1;
+    const int nodes = NP * NP * NP;
+    const long long ks = zm3d_plane_stride(n);
+    const T* Cz = a.face;
+    T inv_eps = T(0);
+    if (M != Mode::F) inv_eps = inv_eps_of<T>(a.eps);
+    ChebK<T> ck = {T(0), T(0), T(0)};
+    if (M == Mode::CHEB0 || M == Mode::CHEB || M == Mode::CHEBLAST) ck = cheb_of<T>(a.cheb, a.cheb_step);
+    float red = 0.f;
+    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < nodes; idx += gridDim.x * blockDim.x) {
+        const int X = idx % NP, YZ = idx / NP;
+        const int Y = YZ % NP, Z = YZ / NP;
+        const bool inner = X > 0 && X < n && Y > 0 && Y < n && Z > 0 && Z < n;
+        T val = T(0);
+        if (inner) {
+            const T* Cp = Cz + JFNK_IDX((long long)Z * n * n + (Y - 1) * n + X - 1, ks - n - 1) + n + 1;
+            const T c0 = Cp[0], c1 = Cp[ks - 1];
+            const T c2 = Cp[2 * ks - n], c3 = Cp[3 * ks - n - 1];
+            val = ((c0 + c1) + (c2 + c3)) * a.node_scale;
+        }
+        epilogue<T, M>(a, idx, inner, val, inv_eps, ck, red);
     }
     stencil_reduce(a, red, red_sm);
 }
@@ -234,6 +397,24 @@ static jfnk_status launch_ep3d_pm(const StencilArgs<T>& a, cudaStream_t st) {
     }
     // x-rows of up to 128 elements per block (a whole number of warps)
     const int bx = std::min(kEpElemThreads, ((g.n + 31) / 32) * 32);
+    if (!ADJ && a.zm_min_n > 0 && g.n >= a.zm_min_n && 4 * zm3d_plane_stride(g.n) <= a.face_cap) {
+        // z chunks so that enough threads march at once: about 39k (8 warps
+        // per SM) in FP64, whose element arithmetic alone keeps the FP64 pipe
+        // busy, and 156k (32 warps per SM) in FP32, where the loads of the next
+        // plane have to be hidden behind other warps' arithmetic
+        const long long cols = (long long)g.n * g.n;
+        const long long target = sizeof(T) == 8 ? 38912 : 155648;
+        const int chunks = (int)std::max<long long>(1, std::min<long long>(g.n, (target + cols - 1) / cols));
+        const int zchunk = (g.n + chunks - 1) / chunks;
+        const int nzc = (g.n + zchunk - 1) / zchunk;
+        zm3d_elem_kernel<T, P, M><<<dim3((g.n + bx - 1) / bx, g.n, nzc), bx, 0, st>>>(a, zchunk);
+        JFNK_LAUNCH_CHECK();
+        const long long nodes = (long long)(g.n + 1) * (g.n + 1) * (g.n + 1);
+        const int nb = (int)std::min<long long>((nodes + kEpNodeThreads - 1) / kEpNodeThreads, 2LL * kMaxRedBlocks);
+        zm3d_node_kernel<T, M><<<nb, kEpNodeThreads, 0, st>>>(a);
+        JFNK_LAUNCH_CHECK();
+        return JFNK_OK;
+    }
     ep3d_elem_kernel<T, P, M, ADJ><<<dim3((g.n + bx - 1) / bx, g.n, g.n), bx, 0, st>>>(a);
     JFNK_LAUNCH_CHECK();
     // the reduction scratch holds 2 kMaxRedBlocks partials: nodes grid-strided beyond

@@ -28,6 +28,9 @@
 #include "stencil.cuh"
 #include "stencil_v2.cuh"
 
+// face-buffer index, checked against the buffer in bounds-checked builds
+#define JFNK_IDX_FACE(i) JFNK_IDX((i), a.face_cap)
+
 namespace jfnk {
 
 template <typename T>
@@ -62,6 +65,7 @@ __device__ __forceinline__ ChebK2<float> cheb_of2<float>(const ChebTable* t, int
 template <typename T, Mode M>
 __device__ __forceinline__ void epilogue2(const StencilArgs<T>& a, int idx, bool inner, T val, T inv_eps,
                                           const ChebK2<T>& ck, float& red) {
+    idx = (int)JFNK_IDX(idx, a.g.size);
     if (M == Mode::F) {
         T f = T(0), av = T(0);
         if (inner) {
@@ -144,6 +148,7 @@ __device__ __forceinline__ void epi_load(const StencilArgs<T>& a, int idx, EpiIn
 template <typename T, Mode M>
 __device__ __forceinline__ void epilogue2_pf(const StencilArgs<T>& a, int idx, T val, T inv_eps,
                                              const ChebK2<T>& ck, const EpiIn<T>& e, float& red) {
+    idx = (int)JFNK_IDX(idx, a.g.size - 1);
     if (M == Mode::F) {
         const T f = val - (T)a.load_const - e.ld;
         a.out[idx] = f;
@@ -219,7 +224,7 @@ __global__ void __launch_bounds__(kV2Threads, 1) stencil3d_v2_kernel(const Stenc
 
     // nodal value of w = x + eps v at (x, y, z); boundary entries of v ignored
     auto node_val = [&](int x, int y, int z) -> T {
-        const int idx = (int)z * sz32 + (int)y * sy32 + x;
+        const int idx = (int)JFNK_IDX((int)z * sz32 + (int)y * sy32 + x, g.size);
         T val = a.u[idx];
         if (M != Mode::F) {
             const bool bnd = x == 0 || x == n || y == 0 || y == n || z == 0 || z == n;
@@ -318,9 +323,9 @@ __global__ void __launch_bounds__(kV2Threads, 1) stencil3d_v2_kernel(const Stenc
             if (k == 0 || bndA || tx == 0) {
                 epilogue2<T, M>(a, idx, false, zero, inv_eps, ck0, red);
             } else if (faceA) {
-                a.face[ylo_idx(q, ty, c, k - z0, tx)] = vA;
+                a.face[JFNK_IDX_FACE(ylo_idx(q, ty, c, k - z0, tx))] = vA;
             } else if (k == z0) {
-                a.face[zlo_idx(q, ty, c, w, tx)] = vA;
+                a.face[JFNK_IDX_FACE(zlo_idx(q, ty, c, w, tx))] = vA;
             } else {
                 epilogue2_pf<T, M>(a, idx, vA * scale, inv_eps, ck0, eA, red);
             }
@@ -333,7 +338,7 @@ __global__ void __launch_bounds__(kV2Threads, 1) stencil3d_v2_kernel(const Stenc
             if (k == 0 || bndB || tx == 0) {
                 epilogue2<T, M>(a, idx, false, zero, inv_eps, ck0, red);
             } else {
-                a.face[yhi_idx(q, ty, c, k - z0, tx)] = vB;
+                a.face[JFNK_IDX_FACE(yhi_idx(q, ty, c, k - z0, tx))] = vB;
             }
             if (extra_col) epilogue2<T, M>(a, idx + 1, false, zero, inv_eps, ck0, red);
             carryB = hiB;
@@ -345,9 +350,9 @@ __global__ void __launch_bounds__(kV2Threads, 1) stencil3d_v2_kernel(const Stenc
         if (z1 == n || bndA || tx == 0) {
             epilogue2<T, M>(a, idx, false, zero, inv_eps, ck0, red);
         } else if (faceA) {
-            a.face[ylo_idx(q, ty, c, z1 - z0, tx)] = carryA;
+            a.face[JFNK_IDX_FACE(ylo_idx(q, ty, c, z1 - z0, tx))] = carryA;
         } else {
-            a.face[zhi_idx(q, ty, c, w, tx)] = carryA;
+            a.face[JFNK_IDX_FACE(zhi_idx(q, ty, c, w, tx))] = carryA;
         }
         if (extra_col) epilogue2<T, M>(a, idx + 1, false, zero, inv_eps, ck0, red);
         if (extra_row) {
@@ -355,7 +360,7 @@ __global__ void __launch_bounds__(kV2Threads, 1) stencil3d_v2_kernel(const Stenc
             if (z1 == n || bndB || tx == 0) {
                 epilogue2<T, M>(a, idxB, false, zero, inv_eps, ck0, red);
             } else {
-                a.face[yhi_idx(q, ty, c, z1 - z0, tx)] = carryB;
+                a.face[JFNK_IDX_FACE(yhi_idx(q, ty, c, z1 - z0, tx))] = carryB;
             }
             if (extra_col) epilogue2<T, M>(a, idxB + 1, false, zero, inv_eps, ck0, red);
         }
@@ -405,7 +410,7 @@ __global__ void __launch_bounds__(kV3Threads, MINB) stencil3d_v3_kernel(const St
     if (M == Mode::CHEB0 || M == Mode::CHEB || M == Mode::CHEBLAST) ck = cheb_of2<float>(a.cheb, a.cheb_step);
 
     auto node_val = [&](int x, int y, int z) -> float {
-        const int idx = z * sz32 + y * sy32 + x;
+        const int idx = (int)JFNK_IDX(z * sz32 + y * sy32 + x, g.size);
         float val = a.u[idx];
         if (M != Mode::F) {
             const bool bnd = x == 0 || x == n || y == 0 || y == n || z == 0 || z == n;
@@ -529,12 +534,12 @@ __global__ void __launch_bounds__(kV3Threads, MINB) stencil3d_v3_kernel(const St
                 zero_node(idxA + 1);
             } else if (faceA) {
                 if (x0 == 0) zero_node(idxA);
-                else a.face[ylo_idx(q, ty, c, k - z0, x0)] = v0;
-                a.face[ylo_idx(q, ty, c, k - z0, x0 + 1)] = v1;
+                else a.face[JFNK_IDX_FACE(ylo_idx(q, ty, c, k - z0, x0))] = v0;
+                a.face[JFNK_IDX_FACE(ylo_idx(q, ty, c, k - z0, x0 + 1))] = v1;
             } else if (k == z0) {
                 if (x0 == 0) zero_node(idxA);
-                else a.face[zlo_idx(q, ty, c, w, x0)] = v0;
-                a.face[zlo_idx(q, ty, c, w, x0 + 1)] = v1;
+                else a.face[JFNK_IDX_FACE(zlo_idx(q, ty, c, w, x0))] = v0;
+                a.face[JFNK_IDX_FACE(zlo_idx(q, ty, c, w, x0 + 1))] = v1;
             } else {
                 if (x0 == 0) zero_node(idxA);
                 else epilogue2_pf<float, M>(a, idxA, v0 * scale, inv_eps, ck0, e0, red);
@@ -552,8 +557,8 @@ __global__ void __launch_bounds__(kV3Threads, MINB) stencil3d_v3_kernel(const St
                 zero_node(idx + 1);
             } else {
                 if (x0 == 0) zero_node(idx);
-                else a.face[yhi_idx(q, ty, c, k - z0, x0)] = v0;
-                a.face[yhi_idx(q, ty, c, k - z0, x0 + 1)] = v1;
+                else a.face[JFNK_IDX_FACE(yhi_idx(q, ty, c, k - z0, x0))] = v0;
+                a.face[JFNK_IDX_FACE(yhi_idx(q, ty, c, k - z0, x0 + 1))] = v1;
             }
             if (extra_col) zero_node(idx + 2);
             carryB = hiB;
@@ -569,12 +574,12 @@ __global__ void __launch_bounds__(kV3Threads, MINB) stencil3d_v3_kernel(const St
             zero_node(idx + 1);
         } else if (faceA) {
             if (x0 == 0) zero_node(idx);
-            else a.face[ylo_idx(q, ty, c, z1 - z0, x0)] = v0;
-            a.face[ylo_idx(q, ty, c, z1 - z0, x0 + 1)] = v1;
+            else a.face[JFNK_IDX_FACE(ylo_idx(q, ty, c, z1 - z0, x0))] = v0;
+            a.face[JFNK_IDX_FACE(ylo_idx(q, ty, c, z1 - z0, x0 + 1))] = v1;
         } else {
             if (x0 == 0) zero_node(idx);
-            else a.face[zhi_idx(q, ty, c, w, x0)] = v0;
-            a.face[zhi_idx(q, ty, c, w, x0 + 1)] = v1;
+            else a.face[JFNK_IDX_FACE(zhi_idx(q, ty, c, w, x0))] = v0;
+            a.face[JFNK_IDX_FACE(zhi_idx(q, ty, c, w, x0 + 1))] = v1;
         }
         if (extra_col) zero_node(idx + 2);
         if (extra_row) {
@@ -585,8 +590,8 @@ __global__ void __launch_bounds__(kV3Threads, MINB) stencil3d_v3_kernel(const St
                 zero_node(idxB + 1);
             } else {
                 if (x0 == 0) zero_node(idxB);
-                else a.face[yhi_idx(q, ty, c, z1 - z0, x0)] = v0;
-                a.face[yhi_idx(q, ty, c, z1 - z0, x0 + 1)] = v1;
+                else a.face[JFNK_IDX_FACE(yhi_idx(q, ty, c, z1 - z0, x0))] = v0;
+                a.face[JFNK_IDX_FACE(yhi_idx(q, ty, c, z1 - z0, x0 + 1))] = v1;
             }
             if (extra_col) zero_node(idxB + 2);
         }
@@ -624,10 +629,10 @@ __global__ void __launch_bounds__(256) stencil3d_fixup_kernel(const StencilArgs<
             y = tyb * BY;
             const int cz = z / ZC, zl = z - cz * ZC;
             if (zl != 0) {
-                total = a.face[yhi_idx(q, tyb - 1, cz, zl, x)] + a.face[ylo_idx(q, tyb, cz, zl, x)];
+                total = a.face[JFNK_IDX_FACE(yhi_idx(q, tyb - 1, cz, zl, x))] + a.face[JFNK_IDX_FACE(ylo_idx(q, tyb, cz, zl, x))];
             } else {
-                total = (a.face[yhi_idx(q, tyb - 1, cz - 1, ZC, x)] + a.face[ylo_idx(q, tyb, cz - 1, ZC, x)]) +
-                        (a.face[yhi_idx(q, tyb - 1, cz, 0, x)] + a.face[ylo_idx(q, tyb, cz, 0, x)]);
+                total = (a.face[JFNK_IDX_FACE(yhi_idx(q, tyb - 1, cz - 1, ZC, x))] + a.face[JFNK_IDX_FACE(ylo_idx(q, tyb, cz - 1, ZC, x))]) +
+                        (a.face[JFNK_IDX_FACE(yhi_idx(q, tyb - 1, cz, 0, x))] + a.face[JFNK_IDX_FACE(ylo_idx(q, tyb, cz, 0, x))]);
             }
         } else {
             const int j = i - countA;
@@ -638,7 +643,7 @@ __global__ void __launch_bounds__(256) stencil3d_fixup_kernel(const StencilArgs<
             y = (yi / (BY - 1)) * BY + (yi % (BY - 1)) + 1;
             z = cb * ZC;
             const int tyy = y / BY, ww = y - tyy * BY;
-            total = a.face[zhi_idx(q, tyy, cb - 1, ww, x)] + a.face[zlo_idx(q, tyy, cb, ww, x)];
+            total = a.face[JFNK_IDX_FACE(zhi_idx(q, tyy, cb - 1, ww, x))] + a.face[JFNK_IDX_FACE(zlo_idx(q, tyy, cb, ww, x))];
         }
         const int idx = (int)z * sz32 + (int)y * sy32 + x;
         epilogue2<T, M>(a, idx, true, total * a.node_scale, inv_eps, ck, red);

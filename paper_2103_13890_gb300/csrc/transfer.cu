@@ -30,11 +30,15 @@ __global__ void restrict_kernel(Grid gc, Grid gf, const T* __restrict__ f, T* __
         grid_coords(gc, i, x, y, z);
         const bool bnd = x == 0 || x == gc.nx - 1 || y == 0 || y == gc.ny - 1 ||
                          (gc.d == 3 && (z == 0 || z == gc.nz - 1));
-        const long long fc = (gc.d == 3 ? (long long)(2 * z) * gf.sz : 0) + (long long)(2 * y) * gf.sy + 2 * x;
+        const long long fc = JFNK_IDX((gc.d == 3 ? (long long)(2 * z) * gf.sz : 0) + (long long)(2 * y) * gf.sy + 2 * x,
+                                      gf.size);
         if (bnd) {
             c[i] = inject_boundary ? f[fc] : T(0);
             continue;
         }
+        // the 3^d fine neighbours of an interior coarse node
+        (void)JFNK_IDX(fc - (gc.d == 3 ? gf.sz : 0) - gf.sy - 1, gf.size);
+        (void)JFNK_IDX(fc + (gc.d == 3 ? gf.sz : 0) + gf.sy + 1, gf.size);
         T acc = T(0);
         if (gc.d == 2) {
 #pragma unroll
@@ -96,7 +100,8 @@ __global__ void prolong_add_kernel(Grid gf, Grid gc, const T* __restrict__ c, T*
                 for (int q = 0; q < nxs; ++q) {
                     const bool xb = ix[q] == 0 || ix[q] == gc.nx - 1;
                     if (zb || yb || xb) continue;
-                    acc += wz[a] * wy[b] * wx[q] * c[(long long)iz[a] * gc.sz + (long long)iy[b] * gc.sy + ix[q]];
+                    acc += wz[a] * wy[b] * wx[q] *
+                           c[JFNK_IDX((long long)iz[a] * gc.sz + (long long)iy[b] * gc.sy + ix[q], gc.size)];
                 }
             }
         }

@@ -50,11 +50,12 @@ __global__ void masked_stat_kernel(Grid g, const T* x, int what, double* out, do
 // Scalar grids (nc = 1): the interior is (n-1)^(d-1) rows of n-1 contiguous
 // entries.  One warp per row, lanes along x, rows dealt to warps in a fixed
 // order (reproducible sums); one integer division per row instead of two per
-// entry.  FP32 vectors are summed in FP32 over at most 8 entries per lane and
-// row, then in FP64 (the FP64 pipe runs at 1/64 of the FP32 rate on this GPU,
-// so converting every entry to FP64 made these reductions ALU-bound).
+// entry, and one floating-point operation per entry.  FP32 vectors are summed
+// in FP32 within a row, then in FP64.  (The FP64 pipe runs at 1/64 of the
+// FP32 rate on this GPU: converting every entry to FP64, or FP64 compares and
+// predicated-off FP64 instructions of an unrolled loop, made these reductions
+// bound by that pipe.)
 constexpr int kRowWarps = kVecThreads / 32;
-constexpr int kRowUnroll = 8;
 
 __host__ __device__ __forceinline__ long long interior_rows(const Grid& g) {
     const long long m = g.n - 1;
@@ -69,40 +70,46 @@ __device__ __forceinline__ long long interior_row_base(const Grid& g, unsigned i
     return (long long)(zz + 1) * g.sz + (long long)(yy + 1) * g.sy;
 }
 
-template <typename T>
-__device__ __forceinline__ double row_stat(const T* __restrict__ row, int nx, int lane, int what) {
-    double acc = 0.0;
-    for (int x0 = 1 + lane; x0 < nx - 1; x0 += 32 * kRowUnroll) {
-        T f = T(0);
-#pragma unroll
-        for (int k = 0; k < kRowUnroll; ++k) {
-            const int x = x0 + 32 * k;
-            if (x < nx - 1) {
-                const T v = row[x];
-                f += (what == 0) ? (v < T(0) ? -v : v) : v * v;
-            }
-        }
-        acc += (double)f;
+// |v| without a floating-point instruction (the FP64 pipe is the scarce one)
+__device__ __forceinline__ double abs_bits(double v) {
+    return __longlong_as_double(__double_as_longlong(v) & 0x7fffffffffffffffLL);
+}
+__device__ __forceinline__ float abs_bits(float v) { return __int_as_float(__float_as_int(v) & 0x7fffffff); }
+
+// Sum over the interior entries x = 1 .. nx-2 of one row taken by lane `lane`
+// (every 32nd entry): |v| (WHAT = 0) or v^2 (WHAT = 1).  Exactly one
+// floating-point operation per entry; FP32 rows are summed in FP32 (at most
+// 16 entries a lane up to n = 512), then added in FP64.
+template <typename T, int WHAT>
+__device__ __forceinline__ double row_stat(const T* __restrict__ row, int nx, int lane) {
+    T f = T(0);
+#pragma unroll 4
+    for (int x = 1 + lane; x < nx - 1; x += 32) {
+        const T v = row[x];
+        if (WHAT == 0)
+            f += abs_bits(v);
+        else
+            f = fma(v, v, f);
     }
-    return acc;
+    return (double)f;
 }
 
-template <typename T>
-__global__ void __launch_bounds__(kVecThreads) masked_stat_rows_kernel(Grid g, const T* __restrict__ x, int what,
-                                                                       double* out, double* partials,
-                                                                       unsigned int* counter, EpsParams ep,
-                                                                       EpsSlot* slot, double* norm_out) {
+template <typename T, int WHAT>
+__global__ void __launch_bounds__(kVecThreads) masked_stat_rows_kernel(Grid g, const T* __restrict__ x, double* out,
+                                                                       double* partials, unsigned int* counter,
+                                                                       EpsParams ep, EpsSlot* slot,
+                                                                       double* norm_out) {
     __shared__ double sm[32];
     const int lane = threadIdx.x & 31;
     const unsigned int nrows = (unsigned int)interior_rows(g);
     const unsigned int wstride = gridDim.x * kRowWarps;
     double acc = 0.0;
     for (unsigned int r = blockIdx.x * kRowWarps + (threadIdx.x >> 5); r < nrows; r += wstride)
-        acc += row_stat<T>(x + interior_row_base(g, r), g.nx, lane, what);
+        acc += row_stat<T, WHAT>(x + JFNK_IDX(interior_row_base(g, r), g.size - g.nx + 1), g.nx, lane);
     double bs = block_sum(acc, sm);
     double tot = 0.0;
     if (grid_sum_last(bs, partials, counter, &tot, sm) && threadIdx.x == 0) {
-        double res = (what == 0) ? tot : sqrt(tot);
+        double res = (WHAT == 0) ? tot : sqrt(tot);
         if (out) *out = res;
         if (norm_out) *norm_out = res;
         if (slot) set_eps_slot(slot, ep, res, ep.unit != 0, nullptr);
@@ -118,8 +125,13 @@ template <typename T>
 static jfnk_status launch_masked_stat(const Grid& g, const T* x, int what, double* out, const EpsParams& ep,
                                       EpsSlot* slot, double* norm_out, RedScratch* red, cudaStream_t st) {
     if (g.nc == 1 && !g.beam && g.n >= 2 && g.size <= 0x7fffffffLL) {
-        masked_stat_rows_kernel<T><<<row_blocks(interior_rows(g)), kVecThreads, 0, st>>>(
-            g, x, what, out, red->partial, &red->counter[0], ep, slot, norm_out);
+        const int nb = row_blocks(interior_rows(g));
+        if (what == 0)
+            masked_stat_rows_kernel<T, 0><<<nb, kVecThreads, 0, st>>>(g, x, out, red->partial, &red->counter[0], ep,
+                                                                      slot, norm_out);
+        else
+            masked_stat_rows_kernel<T, 1><<<nb, kVecThreads, 0, st>>>(g, x, out, red->partial, &red->counter[0], ep,
+                                                                      slot, norm_out);
     } else {
         masked_stat_kernel<T><<<vec_blocks(g.size), kVecThreads, 0, st>>>(g, x, what, out, red->partial,
                                                                           &red->counter[0], ep, slot, norm_out);
@@ -150,6 +162,17 @@ template jfnk_status norm_to_eps<double>(const Grid&, const double*, const EpsPa
 // ---------------------------------------------------------------------------
 // multi-dot: blockIdx.y selects a group of 8 vectors
 constexpr int kDotGroup = 8;
+
+template <int NG>
+__device__ __forceinline__ void dot_group(const double* __restrict__ w, const double* __restrict__ V, long long ld,
+                                          long long len, double* acc) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < len;
+         i += (long long)gridDim.x * blockDim.x) {
+        const double wi = w[i];
+#pragma unroll
+        for (int k = 0; k < NG; ++k) acc[k] = fma(wi, V[(long long)k * ld + i], acc[k]);
+    }
+}
 __global__ void multi_dot_kernel(const double* __restrict__ w, const double* __restrict__ V, long long ld,
                                  long long len, int m, double* h, double* partials, unsigned int* counter) {
     __shared__ double sm[kDotGroup][32];
@@ -159,12 +182,17 @@ __global__ void multi_dot_kernel(const double* __restrict__ w, const double* __r
     double acc[kDotGroup];
 #pragma unroll
     for (int k = 0; k < kDotGroup; ++k) acc[k] = 0.0;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < len;
-         i += (long long)gridDim.x * blockDim.x) {
-        const double wi = w[i];
-#pragma unroll
-        for (int k = 0; k < kDotGroup; ++k)
-            if (k < ng) acc[k] += wi * V[(long long)(g0 + k) * ld + i];
+    // exactly ng FP64 FMAs per entry (a loop unrolled to kDotGroup with the
+    // surplus predicated off still spends FP64-pipe issue on them)
+    switch (ng) {
+        case 1: dot_group<1>(w, V + (long long)g0 * ld, ld, len, acc); break;
+        case 2: dot_group<2>(w, V + (long long)g0 * ld, ld, len, acc); break;
+        case 3: dot_group<3>(w, V + (long long)g0 * ld, ld, len, acc); break;
+        case 4: dot_group<4>(w, V + (long long)g0 * ld, ld, len, acc); break;
+        case 5: dot_group<5>(w, V + (long long)g0 * ld, ld, len, acc); break;
+        case 6: dot_group<6>(w, V + (long long)g0 * ld, ld, len, acc); break;
+        case 7: dot_group<7>(w, V + (long long)g0 * ld, ld, len, acc); break;
+        default: dot_group<8>(w, V + (long long)g0 * ld, ld, len, acc); break;
     }
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
@@ -488,26 +516,21 @@ __global__ void __launch_bounds__(kVecThreads) cheb_start_zero_rows_kernel(
     for (unsigned int row = blockIdx.x * kRowWarps + (threadIdx.x >> 5); row < nrows; row += wstride) {
         const unsigned int zz = row / (unsigned int)g.ny, yy = row - zz * (unsigned int)g.ny;
         const bool inner_row = yy > 0 && yy < (unsigned int)g.ny - 1 && (g.d == 2 || (zz > 0 && zz < (unsigned int)g.nz - 1));
-        const long long base = (long long)row * g.sy;
+        const long long base = JFNK_IDX((long long)row * g.sy, g.size - g.nx + 1);
         const T* br = b + base;
         T* rr = r + base;
         T* dr = d + base;
-        for (int x0 = lane; x0 < nx; x0 += 32 * kRowUnroll) {
-            T f = T(0);
-#pragma unroll
-            for (int k = 0; k < kRowUnroll; ++k) {
-                const int x = x0 + 32 * k;
-                if (x < nx) {
-                    const bool in = inner_row && x > 0 && x < nx - 1;
-                    const T bv = in ? br[x] : T(0);
-                    const T dv = bv * ti;
-                    rr[x] = bv;
-                    dr[x] = dv;
-                    f += dv * dv;
-                }
-            }
-            acc += (double)f;
+        T f = T(0);
+#pragma unroll 4
+        for (int x = lane; x < nx; x += 32) {
+            const bool in = inner_row && x > 0 && x < nx - 1;
+            const T bv = in ? br[x] : T(0);
+            const T dv = bv * ti;
+            rr[x] = bv;
+            dr[x] = dv;
+            f = fma(dv, dv, f);
         }
+        acc += (double)f;
     }
     double bs = block_sum(acc, sm);
     double tot = 0.0;

@@ -2,7 +2,8 @@
 
     python -m paper_2103_13890_gb300.kernelbench --kind nd3d --n 160 --op smooth --dtype f64
 
-op: residual | jvp | smooth (one Chebyshev application = start + fused steps)
+op: residual | jvp | jvp_auto (the same with the FD step from the Sec. 1 formula:
+    two masked reductions more, over u and v) | smooth (one Chebyshev application = start + fused steps)
     | vcycle | solve (a whole JFNK-MG solve from u0 = 0 to 1e-8, preconditioner
     in --dtype) | batch (the batched solve of 64 uneven 2D Bratu instances,
     sizes from {129^2, 257^2, 513^2} nodes, lambda ~ U[1, 6.5], seed 4)
@@ -30,7 +31,7 @@ def main():
     ap.add_argument("--n", type=int, default=128)
     ap.add_argument("--levels", type=int, default=0, help="0: coarsest level with 4 elements")
     ap.add_argument("--op", default="residual",
-                    choices=["residual", "jvp", "smooth", "vcycle", "solve", "batch", "sweep"])
+                    choices=["residual", "jvp", "jvp_auto", "smooth", "vcycle", "solve", "batch", "sweep"])
     ap.add_argument("--dtype", default="f64", choices=["f64", "f32"])
     ap.add_argument("--reps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
@@ -84,6 +85,8 @@ def run_one(a, restart=30):
             p.residual(uT, out=out)
         elif a.op == "jvp":
             p.jvp(uT, F, vT, out=out, eps=1e-7)
+        elif a.op == "jvp_auto":
+            p.jvp(uT, F, vT, out=out, eps_mode=jf.EPS_PAPER if a.dtype == "f64" else jf.EPS_FP32)
         elif a.op == "smooth":
             s.zero_()
             p.smooth(vT, s, level=levels - 1, nu=1, s_is_zero=True)
@@ -110,8 +113,8 @@ def run_one(a, restart=30):
     elems = n ** d
     w = 8 if a.dtype == "f64" else 4
     nodes = (n + 1) ** d
-    stencils = {"residual": 1, "jvp": 1, "smooth": o.cheb_degree - 1}.get(a.op)
-    words = {"residual": 2 + (1 if a.kind == "nd3d" else 0), "jvp": 4}.get(a.op)
+    stencils = {"residual": 1, "jvp": 1, "jvp_auto": 1, "smooth": o.cheb_degree - 1}.get(a.op)
+    words = {"residual": 2 + (1 if a.kind == "nd3d" else 0), "jvp": 4, "jvp_auto": 6}.get(a.op)
     line = {"kind": a.kind, "n": n, "levels": levels, "op": a.op, "dtype": a.dtype, "ms": ms}
     if a.op == "solve":
         line.update(newton_its=st["newton_its"], fgmres_its=st["linear_its"], converged=st["converged"])

@@ -28,13 +28,18 @@ def rel(a, b):
 
 
 # 3D kernel selection (read when a Problem is created): "ep" runs the
-# element-parallel kernels on every 3D level, "tiled" the halo-free kernel
-# (n a multiple of 32, n >= 64; in FP32 its two-elements-per-thread variant)
-# or the tiled one, "v2" the same with the one-element-per-thread halo-free
-# kernel in FP32 too, "default" the library's choice.
+# element-parallel kernels (one element a thread) on every 3D level, "zm" their
+# z-marching variant (element columns) wherever the element-parallel kernels
+# run (n > 8 in FP32), "tiled" the halo-free kernel (n a multiple of 32,
+# n >= 64; in FP32 its two-elements-per-thread variant) or the tiled one, "v2"
+# the same with the one-element-per-thread halo-free kernel in FP32 too,
+# "default" the library's choice.
 KERNEL_PATHS = {
     "default": {},
-    "ep": {"JFNK_EP3D_MAX_N_F64": "100000", "JFNK_EP3D_MAX_N_F32": "100000"},
+    "ep": {"JFNK_EP3D_MAX_N_F64": "100000", "JFNK_EP3D_MAX_N_F32": "100000", "JFNK_ZM3D_MIN_N_F64": "0",
+           "JFNK_ZM3D_MIN_N_F32": "0"},
+    "zm": {"JFNK_EP3D_MAX_N_F64": "100000", "JFNK_EP3D_MAX_N_F32": "100000", "JFNK_ZM3D_MIN_N_F64": "2",
+           "JFNK_ZM3D_MIN_N_F32": "2"},
     "tiled": {"JFNK_EP3D_MAX_N_F64": "0", "JFNK_EP3D_MAX_N_F32": "0"},
     "v2": {"JFNK_EP3D_MAX_N_F64": "0", "JFNK_EP3D_MAX_N_F32": "0", "JFNK_V3_F32": "0"},
     # the two-elements-per-thread kernel with one / two CTAs per SM in every
@@ -45,7 +50,8 @@ KERNEL_PATHS = {
 
 
 def kernel_path(monkeypatch, path):
-    for k in ("JFNK_EP3D_MAX_N_F64", "JFNK_EP3D_MAX_N_F32", "JFNK_V3_F32"):
+    for k in ("JFNK_EP3D_MAX_N_F64", "JFNK_EP3D_MAX_N_F32", "JFNK_V3_F32", "JFNK_ZM3D_MIN_N_F64",
+              "JFNK_ZM3D_MIN_N_F32"):
         monkeypatch.delenv(k, raising=False)
     for k, v in KERNEL_PATHS[path].items():
         monkeypatch.setenv(k, v)

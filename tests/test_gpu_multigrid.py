@@ -117,8 +117,9 @@ def test_setup_projection_operator_and_power_method(kind, n, levels):
 
 
 @pytest.mark.parametrize("kind,n,levels,path", [("bratu2d", 64, 4, "default"), ("nd3d", 32, 4, "default"),
-                                                ("nd3d", 32, 4, "tiled"), ("nd3d", 64, 5, "default"),
-                                                ("nd3d", 64, 5, "tiled")])
+                                                ("nd3d", 32, 4, "tiled"), ("nd3d", 32, 4, "zm"),
+                                                ("nd3d", 64, 5, "default"), ("nd3d", 64, 5, "tiled"),
+                                                ("nd3d", 64, 5, "zm")])
 @pytest.mark.parametrize("nu,zero", [(1, True), (3, True), (2, False)])
 def test_chebyshev_smoother_parity(kind, n, levels, path, nu, zero, monkeypatch):
     kernel_path(monkeypatch, path)
@@ -136,7 +137,7 @@ def test_chebyshev_smoother_parity(kind, n, levels, path, nu, zero, monkeypatch)
     assert rel(host(s), so) <= _fd_tol(so, se)
 
 
-@pytest.mark.parametrize("path", ["default", "tiled", "v2", "v3two", "ep"])
+@pytest.mark.parametrize("path", ["default", "tiled", "v2", "v3two", "ep", "zm"])
 def test_chebyshev_smoother_fp32_3d(path, monkeypatch):
     """FP32 smoothing on the finest level of a 65^3 hierarchy (on the "tiled"
     path the two-elements-per-thread halo-free kernel, on "v2" the one-element
@@ -156,7 +157,7 @@ def test_chebyshev_smoother_fp32_3d(path, monkeypatch):
         p.smooth(dev(b, torch.float32), s, level=l, nu=nu, s_is_zero=zero)
         so = jfnk.chebyshev(lv[l], init.copy(), lv[l].x, lv[l].Fx, b, nu, o.cheb_degree, lam, o.cheb_lo,
                             o.cheb_hi, mode="fp32")
-        assert rel(host(s), so) <= 2e-3
+        assert rel(host(s), so) <= 1e-3
         _FP32_SMOOTH.setdefault((zero, nu), {})[path] = host(s)
     # every path run so far in this session agrees to the FP32 FD round-off:
     # each action carries ~2^-23 / sqrt(2^-23) = 3.5e-4 relative noise of its own
@@ -186,7 +187,7 @@ def test_coarse_gmres_parity(kind, n, levels):
 
 @pytest.mark.parametrize("kind,n,levels,path", [("bratu2d", 64, 4, "default"), ("nd3d", 32, 4, "default"),
                                                 ("nd3d", 16, 2, "default"), ("nd3d", 64, 5, "default"),
-                                                ("nd3d", 64, 5, "tiled")])
+                                                ("nd3d", 64, 5, "tiled"), ("nd3d", 64, 5, "zm")])
 def test_vcycle_parity(kind, n, levels, path, monkeypatch):
     """One V-cycle of Alg. 1 with the GPU's lambda_l given to the oracle."""
     kernel_path(monkeypatch, path)
@@ -218,7 +219,7 @@ def test_vcycle_fp32_parity_and_contraction(pc):
     bd = dev(b, torch.float64)
     s = host(p.mg_vcycle(bd))
     so = jfnk.mg_vcycle(lv, levels - 1, b, oo)
-    assert rel(s, so) <= (1e-6 if pc == "f64" else 2e-3)
+    assert rel(s, so) <= (1e-6 if pc == "f64" else 1e-3)
 
 
 @pytest.mark.parametrize("pc", ["f64", "f32"])
@@ -242,7 +243,8 @@ def _nd_direct_solution(n):
     return adjoint.newton_direct("nd3d", np.zeros((n + 1,) * 3), load=fem.mms_load(n))[0]
 
 
-@pytest.mark.parametrize("pc,path", [("f64", "default"), ("f32", "default"), ("f64", "tiled"), ("f32", "ep")])
+@pytest.mark.parametrize("pc,path", [("f64", "default"), ("f32", "default"), ("f64", "tiled"), ("f32", "ep"),
+                                     ("f64", "zm"), ("f32", "zm")])
 def test_solve_nd_matches_discrete_solution(pc, path, monkeypatch):
     kernel_path(monkeypatch, path)
     n = 24  # 25^3 nodes, 4 levels down to 3^3 elements (a sparse direct solve at this size is quick)

@@ -44,7 +44,7 @@ def _kappa(n, seed=3):
 CASES = [("bratu2d", 7), ("bratu2d", 64), ("bratu2d", 95), ("bratu2d", 600),
          ("nd3d", 4), ("nd3d", 33), ("nd3d", 40), ("ndk3d", 5), ("ndk3d", 37),
          ("nd3d", 64), ("nd3d", 96), ("ndk3d", 64)]
-PATH_CASES = [(k, n, path) for k, n in CASES for path in ("default", "ep", "tiled")
+PATH_CASES = [(k, n, path) for k, n in CASES for path in ("default", "ep", "zm", "tiled")
               if k != "bratu2d" or path == "default"]
 # the FP32 one-element-per-thread halo-free kernel (the default FP32 kernel on
 # these grids evaluates two elements per thread), and the 129^3 grid in FP32
@@ -76,7 +76,7 @@ def test_residual_fp64_fp32_parity(kind, n, path, dirichlet, monkeypatch):
 
 
 @pytest.mark.parametrize("kind,n,path", [("bratu2d", 512, "default"), ("nd3d", 128, "default"),
-                                         ("nd3d", 128, "tiled"), ("nd3d", 256, "default"),
+                                         ("nd3d", 128, "tiled"), ("nd3d", 128, "ep"), ("nd3d", 256, "default"),
                                          ("ndk3d", 128, "default")])
 def test_residual_full_size_sampled(kind, n, path, monkeypatch):
     """At the full workload sizes: the oracle evaluates F at 60 sampled nodes
@@ -125,9 +125,9 @@ def _oracle_jvp_case(kind, n):
 
 
 @pytest.mark.parametrize("kind,n,path", [("bratu2d", 64, "default"), ("bratu2d", 95, "default"),
-                                         ("nd3d", 33, "default"), ("nd3d", 33, "tiled"),
-                                         ("ndk3d", 20, "default"), ("ndk3d", 20, "tiled"),
-                                         ("nd3d", 64, "default"), ("nd3d", 64, "tiled")])
+                                         ("nd3d", 33, "default"), ("nd3d", 33, "tiled"), ("nd3d", 33, "zm"),
+                                         ("ndk3d", 20, "default"), ("ndk3d", 20, "tiled"), ("ndk3d", 20, "zm"),
+                                         ("nd3d", 64, "default"), ("nd3d", 64, "tiled"), ("nd3d", 96, "default")])
 def test_jvp_fp64_parity(kind, n, path, monkeypatch):
     kernel_path(monkeypatch, path)
     u, v, kap, Jo, bound, Jex = _oracle_jvp_case(kind, n)
@@ -142,7 +142,8 @@ def test_jvp_fp64_parity(kind, n, path, monkeypatch):
 
 
 @pytest.mark.parametrize("kind,n,path", [("bratu2d", 64, "default"), ("nd3d", 33, "default"),
-                                         ("nd3d", 33, "tiled"), ("nd3d", 64, "default"), ("nd3d", 64, "ep"),
+                                         ("nd3d", 33, "tiled"), ("nd3d", 33, "zm"), ("nd3d", 64, "default"),
+                                         ("nd3d", 64, "ep"),
                                          ("nd3d", 64, "tiled"), ("nd3d", 64, "v2"), ("nd3d", 96, "default")])
 def test_jvp_fp32_parity(kind, n, path, monkeypatch):
     """FP32 action with the single-precision step eps = sqrt(2^-23)(1+||u||)/||v||
@@ -157,7 +158,10 @@ def test_jvp_fp32_parity(kind, n, path, monkeypatch):
     Jv = host(p.jvp(ud, Fu, vd, eps_mode=jf().EPS_FP32))
     lv = jfnk.Level(kind, n, 5.0, None, load)
     Jo = jfnk.fd_jv(lv, u, lv.F(u), v, "fp32")
-    assert rel(Jv, Jo) <= 2e-3
+    # the stated FP32 Jv tolerance; the kernels measure 1.6e-4 to 2e-4 here
+    # (FP32 rounding of F(u + eps v) and F(u), 2^-23 each, over the step
+    # eps ~ sqrt(2^-23) (1 + ||u||) / ||v||)
+    assert rel(Jv, Jo) <= 1e-3
 
 
 def test_jvp_explicit_eps_and_zero_direction():
