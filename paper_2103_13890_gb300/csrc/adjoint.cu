@@ -149,7 +149,7 @@ static jfnk_status launch_vjp_k(Mode mode, const StencilArgs<T>& a, cudaStream_t
 
 template <typename T>
 jfnk_status launch_vjp(Prob prob, Mode mode, const StencilArgs<T>& a, cudaStream_t st) {
-    if ((prob == Prob::NDK3 || prob == Prob::ND3) && ep3d_use(a)) return launch_ep3d<T>(prob, mode, true, a, st);
+    if ((prob == Prob::NDK3 || prob == Prob::ND3) && ep3d_use(a, true)) return launch_ep3d<T>(prob, mode, true, a, st);
     if (prob == Prob::NDK3) return launch_vjp_k<T, true>(mode, a, st);
     if (prob == Prob::ND3) return launch_vjp_k<T, false>(mode, a, st);
     set_error("the adjoint operator is implemented for the 3D diffusion problems");

@@ -241,7 +241,10 @@ static size_t plan(P& p, char* base, const jfnk_options* o) {
             face = std::max(face, v3_face_count(g, p.v2_threads32, 2));
         }
         face = std::max(face, beam_scratch_count(g));
+        // (in doubles; an FP32 level's T entries take half as many bytes)
         if (g.n <= std::max(p.ep_max_n64, p.ep_max_n32)) face = std::max(face, ep3d_scratch_count(g));
+        if (p.zm_min_n64 > 0 && g.n >= p.zm_min_n64) face = std::max(face, ep3d_scratch_need(g, true));
+        if (p.zm_min_n32 > 0 && g.n >= p.zm_min_n32) face = std::max(face, (ep3d_scratch_need(g, true) + 1) / 2);
     }
     p.face_bytes = (size_t)face * sizeof(double);
     p.face = face > 0 ? pl.take<char>(p.face_bytes) : nullptr;

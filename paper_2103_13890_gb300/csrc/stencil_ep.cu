@@ -133,24 +133,26 @@ __global__ void __launch_bounds__(kEpNodeThreads) ep3d_node_kernel(const Stencil
 }
 
 // ---------------------------------------------------------------------------
-// z-marching element columns (large FP64 levels).  Thread (x, y) evaluates the
-// elements (x, y, z) for z in its chunk, in order.  Neighbouring elements of a
-// column share a z face: the x/y butterflies of the face's nodal values
+// z-marching element columns.  Thread (x, y) evaluates the elements
+// (x, y, z) for z in its chunk, in order.  Neighbouring elements of a column
+// share a z face: the x/y butterflies of the face's nodal values
 // (elem_nd3_mid's a/b inputs) are computed once per face instead of once per
 // element, and on the test-function side the two elements' face modes are
 // summed before the y and x passes, so each face's 4 node sums leave the
 // thread already added over z.  The column's 4 per-plane node values go to
 // scratch Cz[k][z][y][x] (k = a + 2b: node (x+a, y+b, z)); the node kernel
 // adds the 4 columns around each node.  Against one element per thread this
-// saves 19 of ~183 FP64 operations per node (forward face butterflies, half
-// the nodal w = x + eps v, the y/x passes of one face, 4 of the 7 node adds)
-// and half of the scratch traffic.  A chunk that starts at z0 > 0 evaluates
-// element z0 - 1 once more (only its upper face modes are kept), so every
-// interior plane is completed inside one chunk and written once.
+// saves 19 of ~183 operations per node (forward face butterflies, half the
+// nodal w = x + eps v, the y/x passes of one face, 4 of the 7 node adds) and
+// half of the scratch traffic.  A chunk that starts at z0 > 0 evaluates element
+// z0 - 1 once more (only its upper face modes are kept), so every interior
+// plane is completed inside one chunk and written once.
+// Selected per precision by zm_min_n (off by default: measured against one
+// element a thread it ran 5-20 % slower in FP64 and within +-10 % of the
+// halo-free kernel in FP32; a variant that also added x neighbours through
+// warp shuffles, halving the scratch again, was slower still).
 // ---------------------------------------------------------------------------
 constexpr int kZmThreads = 128;
-
-__host__ __device__ inline long long zm3d_plane_stride(int n) { return (long long)(n + 1) * n * n; }
 
 template <typename T, Prob P, Mode M>
 __global__ void __launch_bounds__(kZmThreads) zm3d_elem_kernel(const StencilArgs<T> a, int zchunk) {
@@ -382,8 +384,9 @@ __global__ void __launch_bounds__(kEpSmallThreads) ep3d_small_kernel(const Stenc
 template <typename T, Prob P, Mode M, bool ADJ>
 static jfnk_status launch_ep3d_pm(const StencilArgs<T>& a, cudaStream_t st) {
     const Grid& g = a.g;
-    if (ep3d_scratch_count(g) > a.face_cap) {
-        set_error("element scratch too small (%lld < %lld)", a.face_cap, ep3d_scratch_count(g));
+    const bool zm = !ADJ && a.zm_min_n > 0 && g.n >= a.zm_min_n;
+    if (ep3d_scratch_need(g, zm) > a.face_cap) {
+        set_error("element scratch too small (%lld < %lld)", a.face_cap, ep3d_scratch_need(g, zm));
         return JFNK_ERR_WORKSPACE;
     }
     if (g.n > 1024) {
@@ -397,7 +400,7 @@ static jfnk_status launch_ep3d_pm(const StencilArgs<T>& a, cudaStream_t st) {
     }
     // x-rows of up to 128 elements per block (a whole number of warps)
     const int bx = std::min(kEpElemThreads, ((g.n + 31) / 32) * 32);
-    if (!ADJ && a.zm_min_n > 0 && g.n >= a.zm_min_n && 4 * zm3d_plane_stride(g.n) <= a.face_cap) {
+    if (zm) {
         // z chunks so that enough threads march at once: about 39k (8 warps
         // per SM) in FP64, whose element arithmetic alone keeps the FP64 pipe
         // busy, and 156k (32 warps per SM) in FP32, where the loads of the next
