@@ -87,7 +87,9 @@ def test_paper_solver_matches_oracle(k):
     lvs = jfnk.build_hyper_hierarchy(k)
     uo, so = jfnk.newton_solve(lvs, u0, jfnk.paper_options(atol_newton=1e-10))
     assert so.converged
-    assert rel(host(u), uo) <= 1e-7
+    # both stop at ||F|| < 1e-10, where the solution is within ~2e-10 of the
+    # converged one (the oracle's own L1 solve at 1e-10 against 1e-13)
+    assert rel(host(u), uo) <= 1e-8
     b = hyper.dirichlet_mask(u0.shape)
     assert np.array_equal(host(u)[b], u0[b])
     q = jf().Problem("beam3d", m, k + 1, options=jf().paper_options())
@@ -108,7 +110,7 @@ def test_fgmres_solve_with_fp32_preconditioner():
     st = p.solve(u)
     assert st["converged"]
     uo, so = jfnk.newton_solve(jfnk.build_hyper_hierarchy(k), u0, jfnk.paper_options(atol_newton=1e-10))
-    assert rel(host(u), uo) <= 1e-7
+    assert rel(host(u), uo) <= 1e-8
 
 
 @pytest.mark.parametrize("amp", [0.1, 0.4])
