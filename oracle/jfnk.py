@@ -37,8 +37,11 @@ Readings (where the paper is silent, or where the default settings differ from i
   * Line search: backtracking with quadratic then cubic interpolation
     (Dennis & Schnabel, Numerical Methods for Unconstrained Optimization and
     Nonlinear Equations, Sec. 6.3) on phi(alpha) = 1/2 ||F(u + alpha dx)||^2,
-    slope phi'(0) = F . (J dx) from one FD action, Armijo constant 1e-4,
-    new step clipped to [0.1, 0.5] alpha, at most 10 backtracks.
+    Armijo constant 1e-4, new step clipped to [0.1, 0.5] alpha, at most 10
+    residual evaluations; without sufficient decrease the step is not taken
+    and the solve stops.  The slope phi'(0) = F . (J dx): after a single
+    FGMRES cycle from the Arnoldi relation of that cycle (the FD actions it
+    already applied), otherwise (restarts, CG) from one more FD action.
   * P x^(k) and F(P x^(k)) on each level are evaluated once per Newton step
     (x^(k) does not change during the step, so this equals re-evaluating
     them inside every cycle as Alg. 1 writes it).
@@ -329,27 +332,39 @@ def _givens(a, b):
     return a / r, b / r
 
 
-def gmres(apply_A, b, mask, tol, maxit, precond=None, restart=None, tol_abs=None):
+def gmres(apply_A, b, mask, tol, maxit, precond=None, restart=None, tol_abs=None, info=None):
     """(F)GMRES with x0 = 0 and modified Gram-Schmidt Arnoldi.
     precond=None: plain GMRES; otherwise right-preconditioned flexible GMRES
     (z_j = M v_j is stored, x = x0 + Z y).  Stops when the Givens residual
     estimate is <= tol * ||b|| (or <= tol_abs when given) or after maxit
     iterations; restart=None means unrestarted.
-    Returns (x, iterations, final residual estimate)."""
+    Returns (x, iterations, final residual estimate).
+
+    info (a dict, optional) receives "cycles" (Arnoldi cycles run) and, from
+    the last cycle, "beta" = ||r|| at its start and "Hy0" = (Hbar y)_0, the
+    first entry of the unrotated (k+1) x k Hessenberg matrix times the
+    least-squares solution.  With one cycle (x0 = 0, v_0 = b / beta) the
+    Arnoldi relation A Z y = V_(k+1) Hbar y gives b . (A x) = beta Hy0 from the
+    actions already applied."""
     x = np.zeros_like(b)
     beta0 = norm_i(b, mask)
     target = tol_abs if tol_abs is not None else tol * beta0
+    if info is not None:
+        info.update(cycles=0, beta=beta0, Hy0=0.0)
     if beta0 == 0.0 or beta0 <= target:
         return x, 0, beta0
     m = restart if restart is not None else maxit
     total = 0
     r = np.where(mask, b, 0.0)
     res = beta0
+    cycles = 0
     while True:
+        cycles += 1
         beta = norm_i(r, mask)
         V = [r / beta]
         Z = []
         H = np.zeros((m + 1, m))
+        Hraw = np.zeros((m + 1, m))
         g = np.zeros(m + 1)
         g[0] = beta
         cs = np.zeros(m)
@@ -363,6 +378,7 @@ def gmres(apply_A, b, mask, tol, maxit, precond=None, restart=None, tol_abs=None
                 H[i, j] = float(np.sum(w[mask] * V[i][mask]))
                 w = w - H[i, j] * V[i]
             H[j + 1, j] = norm_i(w, mask)
+            Hraw[:j + 2, j] = H[:j + 2, j]
             for i in range(j):
                 t = cs[i] * H[i, j] + sn[i] * H[i + 1, j]
                 H[i + 1, j] = -sn[i] * H[i, j] + cs[i] * H[i + 1, j]
@@ -384,6 +400,8 @@ def gmres(apply_A, b, mask, tol, maxit, precond=None, restart=None, tol_abs=None
             y[i] = (g[i] - np.dot(H[i, i + 1:k], y[i + 1:k])) / H[i, i]
         for i in range(k):
             x = x + y[i] * Z[i]
+        if info is not None:
+            info.update(cycles=cycles, beta=beta, Hy0=float(np.dot(Hraw[0, :k], y)))
         if res <= target or total >= maxit:
             return x, total, res
         r = np.where(mask, b - apply_A(x), 0.0)
@@ -678,15 +696,21 @@ def newton_solve(levels, u0, opts):
         Fx = F
         apply_J = lambda v: fd_jv(fine, u, Fx, v, "paper")  # noqa: E731
         mg = lambda v: mg_vcycle(levels, L, v, opts)  # noqa: E731
+        ginfo = {}
         if opts.outer == "cg":
             du, its, _, _ = pcg(apply_J, -F, fine.mask, eta, opts.max_linear, precond=mg)
         else:
             du, its, _ = gmres(apply_J, -F, fine.mask, eta, opts.max_linear, precond=mg,
-                               restart=opts.restart)
+                               restart=opts.restart, info=ginfo)
         st.linear_its += its
         st.lin_hist.append(its)
         if opts.line_search:
-            slope = float(np.sum(F[fine.mask] * fd_jv(fine, u, F, du, "paper")[fine.mask]))
+            if ginfo.get("cycles") == 1:
+                # phi'(0) = F . (J du) from the Arnoldi relation of the single
+                # FGMRES cycle: b = -F = beta v_0, so F . (J Z y) = -beta (Hbar y)_0
+                slope = -ginfo["beta"] * ginfo["Hy0"]
+            else:
+                slope = float(np.sum(F[fine.mask] * fd_jv(fine, u, F, du, "paper")[fine.mask]))
             trials = []
             alpha, Fn, ok = backtrack(fine.F, u, du, F, slope, max_steps=opts.ls_max, trials=trials)
             st.ls_hist.append(len(trials))

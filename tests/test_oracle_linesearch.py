@@ -113,3 +113,28 @@ def test_newton_stops_at_the_last_accepted_iterate_when_the_line_search_fails():
     assert st.newton_its == 1 and st.alpha_hist == [0.0]
     assert np.array_equal(u, np.zeros_like(u))
     assert st.res_hist[0] == st.res_hist[1]
+
+
+@pytest.mark.parametrize("precond", [False, True])
+@pytest.mark.parametrize("its", [1, 4, 9])
+def test_arnoldi_slope_equals_the_direct_product(precond, its):
+    # the line-search slope F . (J dx) after one FGMRES cycle comes from the
+    # Arnoldi relation A Z y = V Hbar y: with b = -F = beta v_0 it is
+    # b . (A x) = beta (Hbar y)_0.  Against the product formed directly with a
+    # dense nonsymmetric A (and a flexible right preconditioner M):
+    rng = np.random.default_rng(11 + its)
+    n = 40
+    A = np.eye(n) * 4.0 + rng.normal(size=(n, n)) * 0.3
+    M = np.eye(n) + rng.normal(size=(n, n)) * 0.05
+    b = rng.normal(size=n)
+    mask = np.ones(n, dtype=bool)
+    info = {}
+    x, k, _ = jfnk.gmres(lambda v: A @ v, b, mask, 1e-30, its, precond=(lambda v: M @ v) if precond else None,
+                         info=info)
+    assert k == its and info["cycles"] == 1
+    direct = float(b @ (A @ x))
+    assert info["beta"] * info["Hy0"] == pytest.approx(direct, rel=1e-12)
+    # with a restart the relation covers only the last cycle
+    info2 = {}
+    jfnk.gmres(lambda v: A @ v, b, mask, 1e-30, 6, restart=3, info=info2)
+    assert info2["cycles"] == 2
