@@ -731,7 +731,8 @@ static jfnk_status bsetup(BCtx& b, const std::vector<int>& S, int newton_step) {
 
 // Lock-step FGMRES(m) for instances S: J(u_i) delta_i = rhs64_i to eta_i ||rhs_i||.
 template <typename T>
-static jfnk_status bfgmres(BCtx& b, const std::vector<int>& S, const std::vector<double>& eta, std::vector<int>& its) {
+static jfnk_status bfgmres(BCtx& b, const std::vector<int>& S, const std::vector<double>& eta, std::vector<int>& its,
+                           std::vector<ArnoldiSlope>& slope) {
     const jfnk_options& o = *b.o;
     const int m = o.restart;
     std::vector<double> hr;
@@ -770,8 +771,9 @@ static jfnk_status bfgmres(BCtx& b, const std::vector<int>& S, const std::vector
         target[i] = eta[q] * beta[i];
         if (beta[i] > 0.0 && beta[i] > target[i]) act.push_back(i);
     }
-    std::vector<std::vector<double>> H(b.B), g(b.B), cs(b.B), sn(b.B);
+    std::vector<std::vector<double>> H(b.B), Hraw(b.B), g(b.B), cs(b.B), sn(b.B);
     std::vector<int> k(b.B, 0);
+    for (int i : S) slope[i] = ArnoldiSlope();
     while (!act.empty()) {
         // V_0 = tmp / beta (beta already in res slot 0)
         {
@@ -785,6 +787,9 @@ static jfnk_status bfgmres(BCtx& b, const std::vector<int>& S, const std::vector
                 v.dsc = b.res + (size_t)i * kResStride;
                 d.push_back(v);
                 H[i].assign((size_t)(m + 1) * m, 0.0);
+                Hraw[i].assign((size_t)(m + 1) * m, 0.0);
+                slope[i].cycles++;
+                slope[i].beta = beta[i];
                 g[i].assign(m + 1, 0.0);
                 cs[i].assign(m, 0.0);
                 sn[i].assign(m, 0.0);
@@ -867,6 +872,7 @@ static jfnk_status bfgmres(BCtx& b, const std::vector<int>& S, const std::vector
                 for (int q = 0; q <= j; ++q) col[q] = rr[1 + q] + rr[1 + (m + 2) + q];
                 const double hn = rr[2 * (m + 2) + 1];
                 col[j + 1] = hn;
+                for (int q = 0; q <= j + 1; ++q) Hraw[i][(size_t)j * (m + 1) + q] = col[q];
                 if (!std::isfinite(hn)) {
                     set_error("non-finite Arnoldi entry in batched FGMRES (instance %d)", i);
                     return JFNK_ERR_NONFINITE;
@@ -918,6 +924,9 @@ static jfnk_status bfgmres(BCtx& b, const std::vector<int>& S, const std::vector
                 y[q] = t / hqq;
             }
             for (int q = 0; q < k[i]; ++q) yall[(size_t)i * kResStride + 1 + q] = y[q];
+            double hy0 = 0.0;
+            for (int q = 0; q < k[i]; ++q) hy0 += Hraw[i][(size_t)q * (m + 1)] * y[q];
+            slope[i].Hy0 = hy0;
         }
         JFNK_CUDA_TRY(cudaMemcpyAsync(b.res, yall.data(), sizeof(double) * yall.size(), cudaMemcpyHostToDevice, b.st));
         {
@@ -1153,24 +1162,34 @@ static jfnk_status bsolve(BCtx& b, jfnk_stats* stats) {
         for (int i : act)
             eta.push_back(o.eta_mode == 1 ? std::fmin(o.eta_max, nF[i]) : std::fmin(o.eta_max, nF[i] / F0[i]));
         std::vector<int> its(B, 0);
-        JFNK_TRY(bfgmres<T>(b, act, eta, its));
+        std::vector<ArnoldiSlope> asl(B);
+        JFNK_TRY(bfgmres<T>(b, act, eta, its, asl));
         for (int i : act) {
             JFNK_TRY(check_status(*b.ps[i], b.st));
             S[i].linear_its += its[i];
             if (k < JFNK_MAX_HIST) S[i].lin_hist[k] = its[i];
         }
-        // line search: slope F . (J delta), then backtracking per instance
+        // line search: slope F . (J delta) -- from the Arnoldi relation after a
+        // single FGMRES cycle, else from one more FD action -- then backtracking
+        // per instance
         std::vector<double> slope(B, 0.0), alpha(B, 1.0), nT(B, 0.0), pa(B, -1.0), pf(B, 0.0);
-        if (o.line_search) {
+        std::vector<int> fd;
+        for (int i : act) {
+            if (asl[i].cycles == 1)
+                slope[i] = -asl[i].beta * asl[i].Hy0;
+            else
+                fd.push_back(i);
+        }
+        if (o.line_search && !fd.empty()) {
             std::vector<const double*> dv;
             std::vector<double*> wv;
-            for (int i : act) {
+            for (int i : fd) {
                 dv.push_back(b.ps[i]->delta);
                 wv.push_back(b.ps[i]->w64);
             }
-            JFNK_TRY(bjv64(b, act, dv, wv));
+            JFNK_TRY(bjv64(b, fd, dv, wv));
             std::vector<BVec> d;
-            for (int i : act) {
+            for (int i : fd) {
                 P& p = *b.ps[i];
                 BVec v = bv0();
                 v.g = p.lv[p.L].g;
@@ -1183,9 +1202,9 @@ static jfnk_status bsolve(BCtx& b, jfnk_stats* stats) {
                 v.counter = &p.counters[2];
                 d.push_back(v);
             }
-            JFNK_TRY(bvec<double>(b, b.dyn, BOp::MDOT, d, sizes_of(b, act, -1)));
+            JFNK_TRY(bvec<double>(b, b.dyn, BOp::MDOT, d, sizes_of(b, fd, -1)));
             JFNK_TRY(read_res(b, hr));
-            for (int i : act) slope[i] = hr[(size_t)i * kResStride + 1];
+            for (int i : fd) slope[i] = hr[(size_t)i * kResStride + 1];
         }
         std::vector<int> search = act;
         std::vector<char> ok(B, 0);

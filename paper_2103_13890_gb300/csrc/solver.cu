@@ -560,7 +560,11 @@ static jfnk_status vcycle_graph(P& p, const jfnk_options& o, cudaStream_t st) {
 
 // x_L = u, x_(l-1) = P x_l, A(x_l), statistics for eps, power method (Sec. 2)
 template <typename T>
-static jfnk_status mg_setup_T(P& p, const jfnk_options& o, const double* u, int newton_step, cudaStream_t st) {
+// au_fine (nullable): A(u) at the finest level, already evaluated in FP64 for
+// this u (the Newton residual); an FP64 hierarchy copies it instead of
+// evaluating the same kernel on the same input again.
+static jfnk_status mg_setup_T(P& p, const jfnk_options& o, const double* u, int newton_step, cudaStream_t st,
+                              const double* au_fine = nullptr) {
     Range rg("mg setup (Newton step %d)", newton_step);
     Level& Lf = p.lv[p.L];
     if (newton_step == 0 && p.lb) {
@@ -576,12 +580,16 @@ static jfnk_status mg_setup_T(P& p, const jfnk_options& o, const double* u, int 
         JFNK_TRY(restrict_to<T>(p.lv[l].g, p.lv[l - 1].g, as<T>(p.lv[l].x), as<T>(p.lv[l - 1].x), true, st));
     for (int l = 0; l <= p.L; ++l) {
         Level& L = p.lv[l];
-        StencilArgs<T> a = base_args<T>(p, l);
-        a.u = as<T>(L.x);
-        a.out = as<T>(L.Ax);
-        JFNK_TRY(launch_stencil<T>(prob_of(p), Mode::F, a, st));
-        p.nF[l]++;
-        p.nFplain[l]++;
+        if (l == p.L && au_fine && sizeof(T) == 8) {
+            JFNK_CUDA_TRY(cudaMemcpyAsync(L.Ax, au_fine, sizeof(double) * L.g.size, cudaMemcpyDeviceToDevice, st));
+        } else {
+            StencilArgs<T> a = base_args<T>(p, l);
+            a.u = as<T>(L.x);
+            a.out = as<T>(L.Ax);
+            JFNK_TRY(launch_stencil<T>(prob_of(p), Mode::F, a, st));
+            p.nF[l]++;
+            p.nFplain[l]++;
+        }
         JFNK_TRY(masked_stat<T>(L.g, as<T>(L.x), 0, L.xstat_paper, p.red, st));
         JFNK_TRY(masked_stat<T>(L.g, as<T>(L.x), 1, L.xstat_fp32, p.red, st));
     }
@@ -720,10 +728,22 @@ static void givens(double a, double b, double& c, double& s) {
     s = b / r;
 }
 
+// What FGMRES leaves for the line-search slope: the Arnoldi cycles run and,
+// from the last cycle, beta = ||r|| at its start and (Hbar y)_0, the first entry
+// of the unrotated Hessenberg matrix times the least-squares solution.  After a
+// single cycle from delta = 0 (v_0 = rhs / beta) the Arnoldi relation
+// J Z y = V Hbar y gives rhs . (J delta) = beta (Hbar y)_0 from the FD actions
+// already applied.
+struct ArnoldiSlope {
+    int cycles = 0;
+    double beta = 0.0, Hy0 = 0.0;
+};
+
 // FGMRES(m): J(u) delta = rhs64 to ||rhs - J delta|| <= eta ||rhs||, right-
 // preconditioned by one V-cycle per iteration.
 template <typename T>
-static jfnk_status fgmres(P& p, const jfnk_options& o, const double* u, double eta, int& its, cudaStream_t st) {
+static jfnk_status fgmres(P& p, const jfnk_options& o, const double* u, double eta, int& its, cudaStream_t st,
+                          ArnoldiSlope* slope = nullptr) {
     const Grid& g = p.lv[p.L].g;
     const long long N = g.size;
     const int m = o.restart;
@@ -740,9 +760,12 @@ static jfnk_status fgmres(P& p, const jfnk_options& o, const double* u, double e
     const double target = eta * beta0;
     JFNK_CUDA_TRY(cudaMemcpyAsync(p.tmp64, p.rhs64, sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
     double beta = beta0;
-    std::vector<double> H((size_t)(m + 1) * m), gv(m + 1), cs(m), sn(m), y(m), hh(2 * (m + 2));
+    std::vector<double> H((size_t)(m + 1) * m), Hraw((size_t)(m + 1) * m), gv(m + 1), cs(m), sn(m), y(m),
+        hh(2 * (m + 2));
     T* Z = as<T>(p.Z);
+    int cycles = 0;
     while (true) {
+        cycles++;
         // V_0 = r / beta
         JFNK_CUDA_TRY(cudaMemcpyAsync(p.scal, &beta, sizeof(double), cudaMemcpyHostToDevice, st));
         JFNK_TRY(scale_by_inv(p.V64, p.tmp64, N, p.scal, st));
@@ -785,6 +808,7 @@ static jfnk_status fgmres(P& p, const jfnk_options& o, const double* u, double e
             double* col = &H[(size_t)j * (m + 1)];
             for (int i = 0; i <= j; ++i) col[i] = hh[i] + hh[(m + 2) + i];
             col[j + 1] = hn;
+            for (int i = 0; i <= j + 1; ++i) Hraw[(size_t)j * (m + 1) + i] = col[i];
             if (!std::isfinite(hn)) {
                 set_error("non-finite Arnoldi entry in FGMRES");
                 return JFNK_ERR_NONFINITE;
@@ -824,6 +848,13 @@ static jfnk_status fgmres(P& p, const jfnk_options& o, const double* u, double e
         }
         JFNK_CUDA_TRY(cudaMemcpyAsync(p.ydev, y.data(), sizeof(double) * k, cudaMemcpyHostToDevice, st));
         JFNK_TRY(combine<T>(p.delta, Z, N, N, k, p.ydev, st));
+        if (slope) {
+            double hy0 = 0.0;
+            for (int q = 0; q < k; ++q) hy0 += Hraw[(size_t)q * (m + 1)] * y[q];
+            slope->cycles = cycles;
+            slope->beta = beta;
+            slope->Hy0 = hy0;
+        }
         if (stop) break;
         // restart: r = rhs - J delta
         JFNK_TRY(jv64(p, u, p.Au64, p.delta, p.w64, st));
@@ -953,17 +984,19 @@ static jfnk_status solve_T(P& p, const jfnk_options& o, double* u, jfnk_stats* s
             set_error("non-finite residual norm at Newton step %d", k);
             break;
         }
-        JFNK_TRY(mg_setup_T<T>(p, o, u, k, st));
+        // p.Au64 holds A(u) of this iterate (the Newton residual's evaluation)
+        JFNK_TRY(mg_setup_T<T>(p, o, u, k, st, p.Au64));
         JFNK_TRY(masked_stat<double>(g, u, 0, p.xstat64, p.red, st));
         const double eta = (o.eta_mode == 1) ? std::fmin(o.eta_max, normF) : std::fmin(o.eta_max, normF / F0);
         JFNK_TRY(axpby<double>(p.rhs64, p.F64, -1.0, 0.0, N, st));
         int its = 0;
+        ArnoldiSlope asl;
         if (o.outer == JFNK_OUTER_CG) {
             int negc = 0;
             JFNK_TRY(pcg<T>(p, o, u, eta, its, negc, st));
             S.outer_negcurv += negc;
         } else {
-            JFNK_TRY(fgmres<T>(p, o, u, eta, its, st));
+            JFNK_TRY(fgmres<T>(p, o, u, eta, its, st, &asl));
         }
         JFNK_TRY(check_status(p, st));
         S.linear_its += its;
@@ -972,11 +1005,18 @@ static jfnk_status solve_T(P& p, const jfnk_options& o, double* u, jfnk_stats* s
         double alpha = 1.0, normT = 0.0;
         Range rg_ls("line search (Newton step %d)", k);
         if (o.line_search) {
-            JFNK_TRY(jv64(p, u, p.Au64, p.delta, p.w64, st));
-            JFNK_TRY(multi_dot(p.F64, p.w64, N, N, 1, p.hbuf, p.dot_partials, &p.counters[2], st));
+            // phi'(0) = F . (J delta): after a single FGMRES cycle from its Arnoldi
+            // relation (rhs = -F = beta v_0, so F . (J Z y) = -beta (Hbar y)_0),
+            // otherwise (restarts, CG) from one more FD action
             double slope = 0.0;
-            JFNK_CUDA_TRY(cudaMemcpyAsync(&slope, p.hbuf, sizeof(double), cudaMemcpyDeviceToHost, st));
-            JFNK_CUDA_TRY(cudaStreamSynchronize(st));
+            if (asl.cycles == 1) {
+                slope = -asl.beta * asl.Hy0;
+            } else {
+                JFNK_TRY(jv64(p, u, p.Au64, p.delta, p.w64, st));
+                JFNK_TRY(multi_dot(p.F64, p.w64, N, N, 1, p.hbuf, p.dot_partials, &p.counters[2], st));
+                JFNK_CUDA_TRY(cudaMemcpyAsync(&slope, p.hbuf, sizeof(double), cudaMemcpyDeviceToHost, st));
+                JFNK_CUDA_TRY(cudaStreamSynchronize(st));
+            }
             const double f0 = 0.5 * normF * normF;
             double prev_a = -1.0, prev_f = 0.0;
             bool ok = false;

@@ -25,7 +25,7 @@
 namespace jfnk {
 
 constexpr int kEpElemThreads = 128;
-constexpr int kEpNodeThreads = 128;
+constexpr int kEpNodeThreads = 256;
 
 // Element (x, y, z): blockIdx.y = y, blockIdx.z = z, x = blockIdx.x * blockDim.x
 // + threadIdx.x, so a warp holds consecutive elements of one x-row.  Each
