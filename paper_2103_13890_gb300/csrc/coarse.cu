@@ -227,10 +227,10 @@ __device__ void coarse_gmres_body(const CoarseArgs<T>& a, unsigned char* smem_ra
     for (int j = 0; j < m; ++j) {
         const T* vj = V + (long long)j * N;
         // ||v_j|| (unit up to rounding) and the FD step
-        acc = 0.0;
+        T vacc = T(0);
         for (int i = tid; i < N; i += blockDim.x)
-            if (coarse_inner(g, i)) acc += (double)vj[i] * (double)vj[i];
-        double vn2 = block_sum(acc, red);
+            if (coarse_inner(g, i)) vacc += vj[i] * vj[i];
+        double vn2 = block_sum(vacc, red);
         if (tid == 0) {
             double e = eps_formula(a.eps_mode, a.n_unknowns, xstat, sqrt(vn2));
             s_scalar[1] = e;
@@ -254,28 +254,31 @@ __device__ void coarse_gmres_body(const CoarseArgs<T>& a, unsigned char* smem_ra
         // classical Gram-Schmidt, twice; h accumulated in hcol
         for (int i = tid; i <= j; i += blockDim.x) hcol[i] = 0.0;
         __syncthreads();
+        // (dots and updates in the basis precision T: in an FP32 preconditioner the
+        // single CTA would otherwise spend its iterations on this SM's FP64 pipe,
+        // 1/74 of the FP32 rate; the Hessenberg entries are kept in FP64)
         for (int pass = 0; pass < 2; ++pass) {
             for (int q = wid; q <= j; q += nwarps) {
                 const T* vq = V + (long long)q * N;
-                double d = 0.0;
-                for (int i = lane; i < N; i += 32) d += (double)wv[i] * (double)vq[i];
+                T d = T(0);
+                for (int i = lane; i < N; i += 32) d += wv[i] * vq[i];
                 d = warp_sum(d);
                 if (lane == 0) {
-                    hcol[q] += d;
-                    H[(long long)j * (m + 1) + q] = d;
+                    hcol[q] += (double)d;
+                    H[(long long)j * (m + 1) + q] = (double)d;
                 }
             }
             __syncthreads();
             for (int i = tid; i < N; i += blockDim.x) {
-                double w = (double)wv[i];
-                for (int q = 0; q <= j; ++q) w -= H[(long long)j * (m + 1) + q] * (double)V[(long long)q * N + i];
-                wv[i] = (T)w;
+                T w = wv[i];
+                for (int q = 0; q <= j; ++q) w -= (T)H[(long long)j * (m + 1) + q] * V[(long long)q * N + i];
+                wv[i] = w;
             }
             __syncthreads();
         }
-        acc = 0.0;
-        for (int i = tid; i < N; i += blockDim.x) acc += (double)wv[i] * (double)wv[i];
-        double wn2 = block_sum(acc, red);
+        T accT = T(0);
+        for (int i = tid; i < N; i += blockDim.x) accT += wv[i] * wv[i];
+        double wn2 = block_sum(accT, red);
         if (tid == 0) {
             const double hn = sqrt(wn2);
             hcol[j + 1] = hn;
@@ -306,9 +309,9 @@ __device__ void coarse_gmres_body(const CoarseArgs<T>& a, unsigned char* smem_ra
         __syncthreads();
         k = j + 1;
         if (s_flag) break;
-        const double hn = s_scalar[0];
+        const T hinv = (T)(1.0 / s_scalar[0]);
         T* vn = V + (long long)(j + 1) * N;
-        for (int i = tid; i < N; i += blockDim.x) vn[i] = (T)((double)wv[i] / hn);
+        for (int i = tid; i < N; i += blockDim.x) vn[i] = wv[i] * hinv;
         __syncthreads();
     }
     // back-substitution (thread 0), y into gv
@@ -322,9 +325,9 @@ __device__ void coarse_gmres_body(const CoarseArgs<T>& a, unsigned char* smem_ra
     }
     __syncthreads();
     for (int i = tid; i < N; i += blockDim.x) {
-        double sv = 0.0;
-        for (int q = 0; q < k; ++q) sv += gv[q] * (double)V[(long long)q * N + i];
-        a.s[i] = coarse_inner(g, i) ? (T)sv : T(0);
+        T sv = T(0);
+        for (int q = 0; q < k; ++q) sv += (T)gv[q] * V[(long long)q * N + i];
+        a.s[i] = coarse_inner(g, i) ? sv : T(0);
     }
 }
 
