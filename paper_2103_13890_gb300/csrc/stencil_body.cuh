@@ -37,49 +37,77 @@ __device__ __forceinline__ ChebK<float> cheb_of<float>(const ChebTable* t, int i
     return {t->theta_invf, t->c1f[i], t->c2f[i]};
 }
 
+// FP32 square of a value for the norm reductions of the epilogues (the norm
+// feeds the FD step and the power-method estimate, which need far less than
+// FP32 accuracy).  From FP64 the conversion is done on the integer pipe by
+// truncating the significand: on this GPU a hardware FP64 -> FP32 conversion
+// runs on the FP64 pipe, the one the FP64 kernels are bound by.  Magnitudes
+// below 2^-126 give 0; finite magnitudes beyond the FP32 range saturate to the
+// largest finite FP32 value, and a NaN or an infinity gives NaN, so that a
+// non-finite result still reaches the FD-step check.
+__device__ __forceinline__ float sq_for_norm(float v) { return v * v; }
+__device__ __forceinline__ float sq_for_norm(double v) {
+    const long long b = __double_as_longlong(v);
+    const unsigned int hi = (unsigned int)(b >> 32), lo = (unsigned int)b;
+    const unsigned int ed = (hi >> 20) & 0x7ffu;
+    int e = (int)ed - 1023 + 127;
+    unsigned int m = ((hi & 0xfffffu) << 3) | (lo >> 29);
+    if (e <= 0) e = 0, m = 0;
+    if (e >= 255) e = 254, m = 0x7fffffu;
+    if (ed == 0x7ffu) e = 255, m = 0x400000u;  // NaN
+    const float f = __int_as_float((int)(((unsigned int)e << 23) | m));
+    return f * f;
+}
+
 // Per-node epilogue.  val = A(w)_i (already scaled).  Boundary nodes get 0 in
 // every output.  `red` accumulates the square of the reduced quantity.
-template <typename T, Mode M>
+// RAW: val is the unscaled node sum S and A(w)_i = S ns; the FD quotient is
+// then formed as S (ns / eps) - A(x)_i / eps with one FMA (ns_inv = ns / eps),
+// one FP64 operation fewer per node for the kernels bound by the FP64 pipe.
+template <typename T, Mode M, bool RAW = false>
 __device__ __forceinline__ void epilogue(const StencilArgs<T>& a, long long idx, bool inner, T val,
-                                         T inv_eps, const ChebK<T>& ck, float& red) {
+                                         T inv_eps, const ChebK<T>& ck, float& red, T ns = T(1),
+                                         T ns_inv = T(0)) {
     idx = JFNK_IDX(idx, a.g.size);
+    // (A(w)_i - A(x)_i) / eps
+    auto fdq = [&](T ax) -> T { return RAW ? fma(val, ns_inv, -(ax * inv_eps)) : (val - ax) * inv_eps; };
     if (M == Mode::F) {
         T f = T(0), av = T(0);
         if (inner) {
-            av = val;
-            f = val - (T)a.load_const;
+            av = RAW ? val * ns : val;
+            f = av - (T)a.load_const;
             if (a.load) f -= a.load[idx];
         }
         a.out[idx] = f;
         if (a.out2) a.out2[idx] = av;
-        red += (float)f * (float)f;
+        red += sq_for_norm(f);
     } else if (M == Mode::JV) {
         // Au may be F(u) = A(u) - load: the same load is then removed from A(w)
         T jv = T(0);
         if (inner) {
-            T aw = val - (T)a.load_const;
-            if (a.load) aw -= a.load[idx];
-            jv = (aw - a.Au[idx]) * inv_eps;
+            T base = a.Au[idx] + (T)a.load_const;
+            if (a.load) base += a.load[idx];
+            jv = fdq(base);
         }
         a.out[idx] = jv;
-        red += (float)jv * (float)jv;
+        red += sq_for_norm(jv);
     } else if (M == Mode::BMJ) {
-        T o = inner ? a.rhs[idx] - (val - a.Au[idx]) * inv_eps : T(0);
+        T o = inner ? a.rhs[idx] - fdq(a.Au[idx]) : T(0);
         a.out[idx] = o;
-        red += (float)o * (float)o;
+        red += sq_for_norm(o);
     } else if (M == Mode::CHEB0) {
         T rr = T(0), dd = T(0);
         if (inner) {
-            rr = a.rhs[idx] - (val - a.Au[idx]) * inv_eps;
+            rr = a.rhs[idx] - fdq(a.Au[idx]);
             dd = rr * ck.theta_inv;
         }
         a.out[idx] = rr;
         a.out2[idx] = dd;
-        red += (float)dd * (float)dd;
+        red += sq_for_norm(dd);
     } else if (M == Mode::CHEB) {
         T rr = T(0), ss = T(0), dn = T(0);
         if (inner) {
-            T jd = (val - a.Au[idx]) * inv_eps;
+            T jd = fdq(a.Au[idx]);
             T dc = a.v[idx];
             rr = a.r[idx] - jd;
             ss = a.s[idx] + dc;
@@ -88,18 +116,18 @@ __device__ __forceinline__ void epilogue(const StencilArgs<T>& a, long long idx,
         a.r[idx] = rr;
         a.s[idx] = ss;
         a.dnew[idx] = dn;
-        red += (float)dn * (float)dn;
+        red += sq_for_norm(dn);
     } else {  // CHEBLAST
         T ss = T(0);
         if (inner) {
-            T jd = (val - a.Au[idx]) * inv_eps;
+            T jd = fdq(a.Au[idx]);
             T dc = a.v[idx];
             T rr = a.r[idx] - jd;
             T dn = ck.c1 * dc + ck.c2 * rr;
             ss = a.s[idx] + dc + dn;
         }
         a.s[idx] = ss;
-        red += (float)ss * (float)ss;
+        red += sq_for_norm(ss);
     }
 }
 
@@ -113,11 +141,11 @@ __device__ __forceinline__ void epilogue_adj(const StencilArgs<T>& a, long long 
     if (M == Mode::JV) {
         const T o = inner ? jd : T(0);
         a.out[idx] = o;
-        red += (float)o * (float)o;
+        red += sq_for_norm(o);
     } else if (M == Mode::BMJ) {
         const T o = inner ? a.rhs[idx] - jd : T(0);
         a.out[idx] = o;
-        red += (float)o * (float)o;
+        red += sq_for_norm(o);
     } else if (M == Mode::CHEB0) {
         T rr = T(0), dd = T(0);
         if (inner) {
@@ -126,7 +154,7 @@ __device__ __forceinline__ void epilogue_adj(const StencilArgs<T>& a, long long 
         }
         a.out[idx] = rr;
         a.out2[idx] = dd;
-        red += (float)dd * (float)dd;
+        red += sq_for_norm(dd);
     } else if (M == Mode::CHEB) {
         T rr = T(0), ss = T(0), dn = T(0);
         if (inner) {
@@ -138,7 +166,7 @@ __device__ __forceinline__ void epilogue_adj(const StencilArgs<T>& a, long long 
         a.r[idx] = rr;
         a.s[idx] = ss;
         a.dnew[idx] = dn;
-        red += (float)dn * (float)dn;
+        red += sq_for_norm(dn);
     } else if (M == Mode::CHEBLAST) {
         T ss = T(0);
         if (inner) {
@@ -148,7 +176,7 @@ __device__ __forceinline__ void epilogue_adj(const StencilArgs<T>& a, long long 
             ss = a.s[idx] + dc + dn;
         }
         a.s[idx] = ss;
-        red += (float)ss * (float)ss;
+        red += sq_for_norm(ss);
     }
 }
 

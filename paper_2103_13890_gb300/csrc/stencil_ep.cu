@@ -107,6 +107,7 @@ __global__ void __launch_bounds__(kEpNodeThreads) ep3d_node_kernel(const Stencil
     const T* C = a.face;
     T inv_eps = T(0);
     if (!ADJ && M != Mode::F) inv_eps = inv_eps_of<T>(a.eps);
+    const T ns = a.node_scale, ns_inv = a.node_scale * inv_eps;
     ChebK<T> ck = {T(0), T(0), T(0)};
     if (M == Mode::CHEB0 || M == Mode::CHEB || M == Mode::CHEBLAST) ck = cheb_of<T>(a.cheb, a.cheb_step);
     float red = 0.f;
@@ -114,7 +115,7 @@ __global__ void __launch_bounds__(kEpNodeThreads) ep3d_node_kernel(const Stencil
         const int X = idx % NP, YZ = idx / NP;
         const int Y = YZ % NP, Z = YZ / NP;
         const bool inner = X > 0 && X < n && Y > 0 && Y < n && Z > 0 && Z < n;
-        T val = T(0);
+        T sum = T(0);
         if (inner) {
             // element with corner c = dx + 2 dy + 4 dz at this node: (X-dx, Y-dy, Z-dz)
             const T* Cn = C + JFNK_IDX(Z * esz + Y * esy + X - esz - esy - 1, ne - esz - esy - 1) + esz + esy + 1;
@@ -122,12 +123,12 @@ __global__ void __launch_bounds__(kEpNodeThreads) ep3d_node_kernel(const Stencil
             const T c2 = Cn[2 * ne - esy], c3 = Cn[3 * ne - esy - 1];
             const T c4 = Cn[4 * ne - esz], c5 = Cn[5 * ne - esz - 1];
             const T c6 = Cn[6 * ne - esz - esy], c7 = Cn[7 * ne - esz - esy - 1];
-            val = (((c0 + c1) + (c2 + c3)) + ((c4 + c5) + (c6 + c7))) * a.node_scale;
+            sum = ((c0 + c1) + (c2 + c3)) + ((c4 + c5) + (c6 + c7));
         }
         if (ADJ)
-            epilogue_adj<T, M>(a, idx, inner, val, ck, red);
+            epilogue_adj<T, M>(a, idx, inner, sum * ns, ck, red);
         else
-            epilogue<T, M>(a, idx, inner, val, inv_eps, ck, red);
+            epilogue<T, M, true>(a, idx, inner, sum, inv_eps, ck, red, ns, ns_inv);
     }
     stencil_reduce(a, red, red_sm);
 }
