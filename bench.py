@@ -78,7 +78,7 @@ FP64_INST_PER_CLK_SM = 2
 # DRAM bytes (read + write) of one fused FP64 Chebyshev step at 129^3 nodes,
 # element + node phase: dram__bytes_read.sum + dram__bytes_write.sum of the two
 # kernels in one ncu capture of the same kernels (profiles/ holds the summary)
-EP_CHEB_N128_TRAFFIC = (33.854720 + 72.553216 + 198.829312 + 28.200960) * 1e6
+EP_CHEB_N128_TRAFFIC = (33.854720 + 72.549632 + 198.806784 + 29.048064) * 1e6
 
 
 def fp64_peak(peaks):
