@@ -116,6 +116,8 @@ __global__ void __launch_bounds__(kVecThreads) masked_stat_rows_kernel(Grid g, c
     }
 }
 
+// at most kVecBlocks blocks (8 per SM); up to 2048 blocks, one row a warp at
+// 129^3, measured slower (30 against 24 us for two FP32 norms at 129^3)
 static int row_blocks(long long rows) {
     long long b = (rows + kRowWarps - 1) / kRowWarps;
     return (int)(b < kVecBlocks ? (b < 1 ? 1 : b) : kVecBlocks);

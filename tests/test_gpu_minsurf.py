@@ -85,3 +85,22 @@ def test_paper_variant_solve(n, levels):
     # both iterates satisfy ||F|| < 1e-6 and so agree to the conditioning of J
     ud, _ = adjoint.newton_direct("minsurf2d", uo)
     assert rel(host(u), ud) <= 1e-4
+
+
+@pytest.mark.parametrize("k", [1, 2, 3, 4, 5])
+def test_paper_variant_counts_match_the_oracle_at_every_level(k):
+    """The paper's solver on the minimal surface at the refinement levels L1..L5
+    (25 * 2^k elements, k + 1 levels; Sec. 3): the Newton and CG counts of the
+    oracle's run of the same algorithm (stored by
+    tests/golden/make_minsurf_counts.py), and its GE to within 3 % (the GPU takes
+    A(u) of the finest level in the set-up from the Newton residual, one
+    evaluation fewer per Newton step)."""
+    from golden import make_minsurf_counts
+    newton, cg, ge = make_minsurf_counts.load()[k]
+    n = 25 * 2 ** k
+    p = jf().Problem("minsurf2d", n, k + 1, options=jf().paper_options())
+    u = dev(fem.minsurf_boundary(n))
+    st = p.solve(u)
+    assert st["converged"]
+    assert st["newton_its"] == newton and st["linear_its"] == cg, (st["newton_its"], st["linear_its"], newton, cg)
+    assert abs(st["ge"] - ge) <= 0.03 * ge, (st["ge"], ge)
