@@ -4,14 +4,17 @@ Workload (one "step" = one complete inexact-Newton solve of the whole hot path):
 3D nonlinear diffusion -div((1+u^2) grad u) = f on the unit cube, Q1 on 129^3
 nodes (2,048,383 unknowns), f manufactured from u* = sin(pi x) sin(pi y)
 sin(pi z), u0 = 0, FP64 throughout, 6-level V(2,2) Chebyshev degree 4 on
-[0.1, 1.1] lambda_max (10 power iterations), GMRES coarse solve, FGMRES(30),
-stop at 1e-8 relative nonlinear residual.
+[0.1, 1.1] lambda_max, GMRES coarse solve, FGMRES(30), stop at 1e-8 relative
+nonlinear residual.  lambda_max by the power method with the stopping rule of
+Sec. 2 (at most 30 iterations, stop once successive estimates differ by less
+than 1e-2 relative; later Newton steps start from the previous eigenvector).
 
 value:   time to solution (s per solve) with inputs resident in HBM.
 e2e:     the same through the C ABI with the initial guess copied from pinned
          host memory and the solution copied back inside the timed region.
-extras:  FP32-preconditioned solve of the same workload (FP32 vs FP64 PC) and
-         residual-evaluation DOF/s with %HBM.
+extras:  FP32-preconditioned solve of the same workload (FP32 vs FP64 PC),
+         the FP64 solve with a fixed 10 power iterations per level and Newton
+         step, and residual-evaluation DOF/s with %HBM.
 roofline: the dominant kernel (the FP64 element-residual kernel with the fused
          Chebyshev epilogue) timed with CUDA events on its stream during K more
          solves right after the timed ones (the value itself is timed without
@@ -46,6 +49,10 @@ WORKLOAD = "nd3d_129^3_fp64_V(2,2)_cheb4_fgmres30_rtol1e-8"
 METRIC = "JFNK-MG time to 1e-8 rel. residual; residual-eval DOF/s (%HBM), FP32 vs FP64 PC"
 # FP64 operations of the sum-factorised Q1 element evaluation (element.cuh)
 ND_OPS_PER_ELEMENT = 164
+# power method of Sec. 2 for the nonlinear-diffusion workloads: at most 30
+# iterations, stop once successive estimates differ by less than 1e-2 relative
+# (the Bratu workloads, single and batched, keep a fixed 10 iterations)
+POWER_RULE = {"power_iters": 30, "power_tol": 1e-2}
 
 
 def max_over_ranks(dist, value):
@@ -157,15 +164,15 @@ def host_info():
 
 def oracle_solve(n=ORACLE_N, levels=ORACLE_LEVELS):
     """One complete oracle JFNK-MG solve of the bench problem at (n+1)^3 nodes
-    with the bench's settings (V(2,2), Chebyshev degree 4, 10 power
-    iterations, FGMRES(30), rtol 1e-8, u0 = 0, FP64); numpy on one thread.
+    with the bench's settings (V(2,2), Chebyshev degree 4, power method by the
+    Sec. 2 rule, FGMRES(30), rtol 1e-8, u0 = 0, FP64); numpy on one thread.
     Returns (seconds, stats)."""
     import numpy as np
 
     from oracle import fem, jfnk
     t0 = time.perf_counter()
     lv = jfnk.build_hierarchy("nd3d", n, levels, load=fem.mms_load(n))
-    o = jfnk.Options(nu_pre=2, nu_post=2, cheb_degree=4, rtol_newton=1e-8)
+    o = jfnk.Options(nu_pre=2, nu_post=2, cheb_degree=4, rtol_newton=1e-8, **POWER_RULE)
     _, st = jfnk.newton_solve(lv, np.zeros((n + 1,) * 3), o)
     return time.perf_counter() - t0, st
 
@@ -190,7 +197,7 @@ def oracle_baseline(reps=2):
 def reference_arm(args):
     """The oracle as the reference arm: every step is one complete oracle solve
     of the bench problem at 33^3 nodes on one host core (the 129^3 solve takes
-    about 10 minutes on one core, too long for a step); the line reports the
+    tens of minutes on one core, too long for a step); the line reports the
     measured seconds per 33^3 solve."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -280,7 +287,7 @@ def adjoint_extra(jf, torch, n, shape, stream):
     from workloads import kappa_field, noise_like
     kap = torch.as_tensor(kappa_field(n, seed=5))
     oa = jf.default_options(nu_pre=2, nu_post=2, cheb_degree=4, rtol_newton=1e-8, pc_dtype=jf.F32,
-                            eps_mode_pc=jf.EPS_FP32)
+                            eps_mode_pc=jf.EPS_FP32, **POWER_RULE)
     pa = jf.Problem("ndk3d", n, LEVELS, kappa=kap, options=oa)
     pa.set_kappa(torch.as_tensor(kappa_field(n, seed=6)))
     u_obs = torch.zeros(shape, dtype=torch.float64, device="cuda")
@@ -346,7 +353,7 @@ def large_extra(jf, torch, stream, hbm):
     for pc, reps in (("f64", 1), ("f32", 2)):
         o = jf.default_options(nu_pre=2, nu_post=2, cheb_degree=4, rtol_newton=1e-8,
                                pc_dtype=jf.F32 if pc == "f32" else jf.F64,
-                               eps_mode_pc=jf.EPS_FP32 if pc == "f32" else jf.EPS_PAPER)
+                               eps_mode_pc=jf.EPS_FP32 if pc == "f32" else jf.EPS_PAPER, **POWER_RULE)
         p = jf.Problem("nd3d", n, levels, options=o)
         u.zero_()
         p.solve(u)
@@ -464,10 +471,10 @@ def main():
     shape = (n + 1,) * 3
     N = (n + 1) ** 3
 
-    def make(pc):
+    def make(pc, power=POWER_RULE):
         o = jf.default_options(nu_pre=2, nu_post=2, cheb_degree=4, rtol_newton=1e-8,
                                pc_dtype=jf.F32 if pc == "f32" else jf.F64,
-                               eps_mode_pc=jf.EPS_FP32 if pc == "f32" else jf.EPS_PAPER)
+                               eps_mode_pc=jf.EPS_FP32 if pc == "f32" else jf.EPS_PAPER, **power)
         return jf.Problem("nd3d", n, LEVELS, options=o), o
 
     p64, o64 = make("f64")
@@ -549,6 +556,21 @@ def main():
     solve_once(p64)
     torch.cuda.synchronize()
     sol_diff = float((u32 - u).norm() / u.norm())
+    del p32
+
+    # ---- the FP64 solve with a fixed 10 power iterations per level ------------
+    p10, _ = make("f64", {"power_iters": 10, "power_tol": 0.0})
+    for _ in range(2):
+        solve_once(p10)
+    torch.cuda.synchronize()
+    e6, e7 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e6.record(stream)
+    for _ in range(args.steps):
+        st10 = solve_once(p10)
+    e7.record(stream)
+    torch.cuda.synchronize()
+    ms10 = e6.elapsed_time(e7) / args.steps
+    del p10
 
     # ---- residual evaluation throughput (DOF/s, %HBM) -------------------------
     peaks, peaks_src = load_peaks()
@@ -622,6 +644,7 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic (manufactured solution, analytic load)",
             "config": {"workload": WORKLOAD, "n_nodes": N, "unknowns": dof, "levels": LEVELS,
+                       "power_method": "Sec. 2 rule: at most 30 iterations, stop at a relative change < 1e-2",
                        "l2": "working set > L2 (FGMRES basis alone 31 x 17 MB)", "parallelism":
                        "replicas" if world > 1 else "single"},
             "solves_per_s": world * 1e3 / ms,
@@ -630,6 +653,10 @@ def main():
             "fp32_pc": {"value": ms32 * 1e-3, "unit": "s", "speedup_vs_fp64": ms / ms32,
                         "newton_its": st32["newton_its"], "fgmres_its": st32["linear_its"],
                         "rel_diff_vs_fp64_solution": sol_diff},
+            "fp64_power10": {"value": ms10 * 1e-3, "unit": "s", "newton_its": st10["newton_its"],
+                             "fgmres_its": st10["linear_its"], "ge": st10["ge"],
+                             "note": "the same FP64 solve with a fixed 10 power iterations per level and "
+                                     "Newton step instead of the Sec. 2 stopping rule"},
             "residual_eval": resid,
             "bratu65": bratu65,
             "fp32_vs_fp64_pc_257": large,

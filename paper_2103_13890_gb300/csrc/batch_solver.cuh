@@ -635,81 +635,122 @@ static jfnk_status bsetup(BCtx& b, const std::vector<int>& S, int newton_step) {
         JFNK_TRY(bstat(b, R, c, 0, xv, o1, {}, {}, sizeof(T) == 8));
         JFNK_TRY(bstat(b, R, c, 1, xv, o2, {}, {}, sizeof(T) == 8));
     }
+    // Power method on every smoothed level of every instance.  Levels and
+    // instances are independent: each round issues one iteration for every
+    // (level, instance) still running, and with the stopping rule on
+    // (power_tol > 0) the host reads all their estimates with one
+    // synchronisation per round and drops each pair once its estimate settles.
+    std::vector<std::vector<int>> Rl(cmax + 1);
     for (int c = 1; c <= cmax; ++c) {
         const std::vector<int> R = subset(c);
-        std::vector<long long> z = sizes_of(b, R, c);
-        auto pv_list = [&]() {
-            std::vector<const void*> v;
-            for (int i : R) v.push_back(b.ps[i]->lv[c].pv);
-            return v;
-        };
-        auto eps_list = [&]() {
-            std::vector<EpsParams> e;
-            for (int i : R) e.push_back(eps_params(*b.ps[i], c, o.eps_mode_pc));
-            return e;
-        };
+        Rl[c] = R;
+        if (R.empty()) continue;
+        const std::vector<long long> z = sizes_of(b, R, c);
+        std::vector<const void*> pv;
+        std::vector<EpsParams> ep;
         std::vector<EpsSlot*> slots;
-        std::vector<double*> n0, n1;
+        std::vector<double*> n0;
+        std::vector<BVec> start, sc;
         for (int i : R) {
-            slots.push_back(b.ps[i]->lv[c].eps_aux);
-            n0.push_back(b.ps[i]->lv[c].nrm0);
-            n1.push_back(b.ps[i]->lv[c].nrm1);
+            Level& L = b.ps[i]->lv[c];
+            pv.push_back(L.pv);
+            ep.push_back(eps_params(*b.ps[i], c, o.eps_mode_pc));
+            slots.push_back(L.eps_aux);
+            n0.push_back(L.nrm0);
+            BVec v = bv0();
+            v.g = L.g;
+            v.y = L.pv;
+            v.key = o.seed + (uint64_t)c * 0xD1B54A32D192ED03ULL;
+            start.push_back(v);
+            BVec w = bv0();
+            w.g = L.g;
+            w.x = w.y = L.pv;
+            w.dsc = L.nrm0;
+            sc.push_back(w);
         }
-        {
-            std::vector<BVec> d;
-            for (int i : R) {
-                P& p = *b.ps[i];
-                BVec v = bv0();
-                v.g = p.lv[c].g;
-                v.y = p.lv[c].pv;
-                v.key = o.seed + (uint64_t)c * 0xD1B54A32D192ED03ULL;
-                d.push_back(v);
-            }
-            if (newton_step == 0 || !b.ps[R[0]]->lv[c].pv_valid) JFNK_TRY(bvec<T>(b, A, BOp::SPLITMIX, d, z));
+        if (newton_step == 0 || !b.ps[R[0]]->lv[c].pv_valid) JFNK_TRY(bvec<T>(b, A, BOp::SPLITMIX, start, z));
+        // v <- v / ||v||
+        JFNK_TRY(bstat(b, R, c, 1, pv, n0, slots, ep, sizeof(T) == 8));
+        JFNK_TRY(bvec<T>(b, A, BOp::SCALE_INV_T, sc, z));
+    }
+    // one iteration on level c for instances Ra: w = J v (FD), lambda = ||w|| / ||v||,
+    // v <- w / ||w||
+    auto iterate = [&](int c, const std::vector<int>& Ra) -> jfnk_status {
+        std::vector<const void*> pv;
+        std::vector<double*> n0;
+        std::vector<EpsSlot*> slots;
+        std::vector<EpsParams> ep;
+        std::vector<BVec> sc;
+        std::vector<long long> z;
+        std::vector<StencilArgs<T>> args;
+        std::vector<BScal> rat;
+        for (int i : Ra) {
+            P& p = *b.ps[i];
+            Level& L = p.lv[c];
+            pv.push_back(L.pv);
+            n0.push_back(L.nrm0);
+            slots.push_back(L.eps_aux);
+            ep.push_back(eps_params(p, c, o.eps_mode_pc));
+            BVec v = bv0();
+            v.g = L.g;
+            v.x = v.y = L.pw;
+            v.dsc = L.nrm1;
+            sc.push_back(v);
+            z.push_back(L.g.size);
+            StencilArgs<T> a = base_args<T>(p, c);
+            a.u = as<T>(L.x);
+            a.v = as<T>(L.pv);
+            a.eps = L.eps_aux;
+            a.Au = as<T>(L.Ax);
+            a.out = as<T>(L.pw);
+            a.red = RedOut::NORM;
+            a.red_norm = L.nrm1;
+            args.push_back(a);
+            p.nF[c]++;
+            BScal r;
+            memset(&r, 0, sizeof(r));
+            r.out = L.lam;
+            r.x = L.nrm1;
+            r.x2 = L.nrm0;
+            rat.push_back(r);
         }
-        auto scale = [&](bool pv_by_n0) {
-            std::vector<BVec> d;
-            for (int i : R) {
-                P& p = *b.ps[i];
-                BVec v = bv0();
-                v.g = p.lv[c].g;
-                v.x = v.y = pv_by_n0 ? p.lv[c].pv : p.lv[c].pw;
-                v.dsc = pv_by_n0 ? p.lv[c].nrm0 : p.lv[c].nrm1;
-                d.push_back(v);
-            }
-            return bvec<T>(b, A, BOp::SCALE_INV_T, d, z);
-        };
-        JFNK_TRY(bstat(b, R, c, 1, pv_list(), n0, slots, eps_list(), sizeof(T) == 8));
-        JFNK_TRY(scale(true));
-        for (int it = 0; it < o.power_iters; ++it) {
-            JFNK_TRY(bstat(b, R, c, 1, pv_list(), n0, slots, eps_list(), sizeof(T) == 8));
-            std::vector<StencilArgs<T>> args;
-            std::vector<BScal> rat;
-            for (int i : R) {
-                P& p = *b.ps[i];
-                Level& L = p.lv[c];
-                StencilArgs<T> a = base_args<T>(p, c);
-                a.u = as<T>(L.x);
-                a.v = as<T>(L.pv);
-                a.eps = L.eps_aux;
-                a.Au = as<T>(L.Ax);
-                a.out = as<T>(L.pw);
-                a.red = RedOut::NORM;
-                a.red_norm = L.nrm1;
-                args.push_back(a);
-                p.nF[c]++;
-                BScal r;
-                memset(&r, 0, sizeof(r));
-                r.out = L.lam;
-                r.x = L.nrm1;
-                r.x2 = L.nrm0;
-                rat.push_back(r);
-            }
-            JFNK_TRY(bstencil<T>(b, A, Mode::JV, R, c, args));
-            JFNK_TRY(bscalar(b, A, BScalar::RATIO, rat));
-            JFNK_TRY(scale(false));
-            for (int i : R) std::swap(b.ps[i]->lv[c].pv, b.ps[i]->lv[c].pw);
+        JFNK_TRY(bstat(b, Ra, c, 1, pv, n0, slots, ep, sizeof(T) == 8));
+        JFNK_TRY(bstencil<T>(b, A, Mode::JV, Ra, c, args));
+        JFNK_TRY(bscalar(b, A, BScalar::RATIO, rat));
+        JFNK_TRY(bvec<T>(b, A, BOp::SCALE_INV_T, sc, z));
+        for (int i : Ra) std::swap(b.ps[i]->lv[c].pv, b.ps[i]->lv[c].pw);
+        return JFNK_OK;
+    };
+    std::vector<std::vector<double>> lam_prev(cmax + 1, std::vector<double>(b.ps.size(), 0.0));
+    std::vector<std::vector<double>> lam_now = lam_prev;
+    for (int it = 0; it < o.power_iters; ++it) {
+        bool any = false;
+        for (int c = 1; c <= cmax; ++c) {
+            if (Rl[c].empty()) continue;
+            any = true;
+            JFNK_TRY(iterate(c, Rl[c]));
         }
+        if (!any) break;
+        if (o.power_tol > 0.0) {
+            for (int c = 1; c <= cmax; ++c)
+                for (int i : Rl[c])
+                    JFNK_CUDA_TRY(cudaMemcpyAsync(&lam_now[c][i], b.ps[i]->lv[c].lam, sizeof(double),
+                                                  cudaMemcpyDeviceToHost, b.st));
+            JFNK_CUDA_TRY(cudaStreamSynchronize(b.st));
+            for (int c = 1; c <= cmax; ++c) {
+                std::vector<int> still;
+                for (int i : Rl[c]) {
+                    const bool done =
+                        it > 0 && std::fabs(lam_now[c][i] - lam_prev[c][i]) < o.power_tol * lam_now[c][i];
+                    lam_prev[c][i] = lam_now[c][i];
+                    if (!done) still.push_back(i);
+                }
+                Rl[c].swap(still);
+            }
+        }
+    }
+    for (int c = 1; c <= cmax; ++c) {
+        const std::vector<int> R = subset(c);
         std::vector<BScal> ct;
         for (int i : R) {
             P& p = *b.ps[i];

@@ -593,11 +593,16 @@ static jfnk_status mg_setup_T(P& p, const jfnk_options& o, const double* u, int 
         JFNK_TRY(masked_stat<T>(L.g, as<T>(L.x), 0, L.xstat_paper, p.red, st));
         JFNK_TRY(masked_stat<T>(L.g, as<T>(L.x), 1, L.xstat_fp32, p.red, st));
     }
+    // Power method on every smoothed level.  The levels are independent, so
+    // iteration i is issued for every level still running before the host
+    // reads their estimates: with the stopping rule on, one synchronisation
+    // per iteration instead of one per level and iteration.  Each level runs
+    // the same kernels in the same order as it would alone.
+    std::vector<int> active;
     for (int l = 1; l <= p.L; ++l) {
         Level& L = p.lv[l];
         const EpsParams ep = eps_params(p, l, o.eps_mode_pc);
         if (newton_step == 0 || !L.pv_valid) JFNK_TRY(splitmix_start<T>(L.g, as<T>(L.pv), o.seed, l, st));
-        double lam_prev = 0.0;
         if (!p.adj) {
             // FD power iteration along unit vectors without normalisation passes:
             // each action takes v/||v|| (RedOut::EPS_UNIT), so lambda = ||J v/||v|| ||
@@ -605,65 +610,61 @@ static jfnk_status mg_setup_T(P& p, const jfnk_options& o, const double* u, int 
             EpsParams epu = ep;
             epu.unit = 1;
             JFNK_TRY(norm_to_eps<T>(L.g, as<T>(L.pv), epu, L.eps_aux, L.nrm0, p.red, st));
-            for (int it = 0; it < o.power_iters; ++it) {
-                StencilArgs<T> a = base_args<T>(p, l);
-                a.u = as<T>(L.x);
-                a.v = as<T>(L.pv);
-                a.eps = L.eps_aux;
-                a.Au = as<T>(L.Ax);
-                a.out = as<T>(L.pw);
-                a.red = RedOut::EPS_UNIT;
-                a.red_norm = L.lam;
-                a.red_eps = L.eps_aux;
-                a.epsp = epu;
-                JFNK_TRY(launch_stencil<T>(prob_of(p), Mode::JV, a, st));
-                p.nF[l]++;
-                void* t = L.pv;
-                L.pv = L.pw;
-                L.pw = t;
-                if (o.power_tol > 0.0) {
-                    double lam = 0.0;
-                    JFNK_CUDA_TRY(cudaMemcpyAsync(&lam, L.lam, sizeof(double), cudaMemcpyDeviceToHost, st));
-                    JFNK_CUDA_TRY(cudaStreamSynchronize(st));
-                    const bool done = it > 0 && std::fabs(lam - lam_prev) < o.power_tol * lam;
-                    lam_prev = lam;
-                    if (done) break;
-                }
-            }
-            L.pv_valid = true;
-            JFNK_TRY(cheb_table(L.lam, o.cheb_lo, o.cheb_hi, o.cheb_degree, L.cheb, p.status, st));
-            continue;
-        }
-        // adjoint operator (exact J^T v): normalise explicitly
-        JFNK_TRY(norm_to_eps<T>(L.g, as<T>(L.pv), ep, L.eps_aux, L.nrm0, p.red, st));
-        JFNK_TRY(scale_inplace_inv<T>(as<T>(L.pv), L.g.size, L.nrm0, st));
-        for (int it = 0; it < o.power_iters; ++it) {
+        } else {
+            // adjoint operator (exact J^T v): normalise explicitly
             JFNK_TRY(norm_to_eps<T>(L.g, as<T>(L.pv), ep, L.eps_aux, L.nrm0, p.red, st));
-            StencilArgs<T> a = base_args<T>(p, l);
-            a.u = as<T>(L.x);
-            a.v = as<T>(L.pv);
-            a.eps = L.eps_aux;
-            a.Au = as<T>(L.Ax);
-            a.out = as<T>(L.pw);
+            JFNK_TRY(scale_inplace_inv<T>(as<T>(L.pv), L.g.size, L.nrm0, st));
+        }
+        active.push_back(l);
+    }
+    auto iterate = [&](int l) -> jfnk_status {
+        Level& L = p.lv[l];
+        StencilArgs<T> a = base_args<T>(p, l);
+        a.u = as<T>(L.x);
+        a.v = as<T>(L.pv);
+        a.eps = L.eps_aux;
+        a.Au = as<T>(L.Ax);
+        a.out = as<T>(L.pw);
+        if (!p.adj) {
+            EpsParams epu = eps_params(p, l, o.eps_mode_pc);
+            epu.unit = 1;
+            a.red = RedOut::EPS_UNIT;
+            a.red_norm = L.lam;
+            a.red_eps = L.eps_aux;
+            a.epsp = epu;
+            JFNK_TRY(launch_stencil<T>(prob_of(p), Mode::JV, a, st));
+        } else {
+            JFNK_TRY(norm_to_eps<T>(L.g, as<T>(L.pv), eps_params(p, l, o.eps_mode_pc), L.eps_aux, L.nrm0, p.red,
+                                    st));
             a.red = RedOut::NORM;
             a.red_norm = L.nrm1;
             JFNK_TRY(launch_op<T>(p, Mode::JV, a, st));
-            p.nF[l]++;
             // lambda = ||J v|| / ||v||; v <- J v / ||J v||
             JFNK_TRY(ratio_scalar(L.lam, L.nrm1, L.nrm0, st));
             JFNK_TRY(scale_inplace_inv<T>(as<T>(L.pw), L.g.size, L.nrm1, st));
-            void* t = L.pv;
-            L.pv = L.pw;
-            L.pw = t;
-            if (o.power_tol > 0.0) {
-                double lam = 0.0;
-                JFNK_CUDA_TRY(cudaMemcpyAsync(&lam, L.lam, sizeof(double), cudaMemcpyDeviceToHost, st));
-                JFNK_CUDA_TRY(cudaStreamSynchronize(st));
-                const bool done = it > 0 && std::fabs(lam - lam_prev) < o.power_tol * lam;
-                lam_prev = lam;
-                if (done) break;
-            }
         }
+        p.nF[l]++;
+        std::swap(L.pv, L.pw);
+        return JFNK_OK;
+    };
+    std::vector<double> lam_prev(p.L + 1, 0.0), lam_now(p.L + 1, 0.0);
+    for (int it = 0; it < o.power_iters && !active.empty(); ++it) {
+        for (int l : active) JFNK_TRY(iterate(l));
+        if (o.power_tol > 0.0) {
+            for (int l : active)
+                JFNK_CUDA_TRY(cudaMemcpyAsync(&lam_now[l], p.lv[l].lam, sizeof(double), cudaMemcpyDeviceToHost, st));
+            JFNK_CUDA_TRY(cudaStreamSynchronize(st));
+            std::vector<int> still;
+            for (int l : active) {
+                const bool done = it > 0 && std::fabs(lam_now[l] - lam_prev[l]) < o.power_tol * lam_now[l];
+                lam_prev[l] = lam_now[l];
+                if (!done) still.push_back(l);
+            }
+            active.swap(still);
+        }
+    }
+    for (int l = 1; l <= p.L; ++l) {
+        Level& L = p.lv[l];
         L.pv_valid = true;
         JFNK_TRY(cheb_table(L.lam, o.cheb_lo, o.cheb_hi, o.cheb_degree, L.cheb, p.status, st));
     }

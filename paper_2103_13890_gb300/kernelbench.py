@@ -37,6 +37,13 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--rtol", type=float, default=1e-8)
     ap.add_argument("--profiler-range", action="store_true")
+    ap.add_argument("--power-iters", type=int, default=30,
+                    help="power-method iterations (at most, with --power-tol > 0)")
+    ap.add_argument("--power-tol", type=float, default=1e-2,
+                    help="stop the power method once successive estimates differ by less than this, "
+                         "relative (Sec. 2: 30 and 1e-2); 0: always --power-iters")
+    ap.add_argument("--batch-power-iters", type=int, default=10, help="--op batch: power-method iterations")
+    ap.add_argument("--batch-power-tol", type=float, default=0.0, help="--op batch: stopping rule (0: off)")
     a = ap.parse_args()
     if a.op == "batch":
         return batch_main(a)
@@ -56,7 +63,8 @@ def run_one(a, restart=30):
     dt = torch.float64 if a.dtype == "f64" else torch.float32
     o = jf.default_options(pc_dtype=jf.F64 if a.dtype == "f64" else jf.F32,
                            eps_mode_pc=jf.EPS_PAPER if a.dtype == "f64" else jf.EPS_FP32,
-                           nu_pre=2, nu_post=2, cheb_degree=4, rtol_newton=a.rtol, restart=restart)
+                           nu_pre=2, nu_post=2, cheb_degree=4, rtol_newton=a.rtol, restart=restart,
+                           power_iters=a.power_iters, power_tol=a.power_tol)
     kappa = None
     if a.kind == "ndk3d":
         g = torch.Generator().manual_seed(0)
@@ -162,7 +170,8 @@ def batch_main(a):
     from workloads import batch_instances
     inst = batch_instances(64, seed=4)
     o = jf.default_options(rtol_newton=1e-8, pc_dtype=jf.F64 if a.dtype == "f64" else jf.F32,
-                           eps_mode_pc=jf.EPS_PAPER if a.dtype == "f64" else jf.EPS_FP32)
+                           eps_mode_pc=jf.EPS_PAPER if a.dtype == "f64" else jf.EPS_FP32,
+                           power_iters=a.batch_power_iters, power_tol=a.batch_power_tol)
     ps = [jf.Problem("bratu2d", nn, int(round(math.log2(nn // 8))) + 1, lam=lam, options=o) for nn, lam in inst]
     us = [torch.zeros((nn + 1, nn + 1), dtype=torch.float64, device="cuda") for nn, _ in inst]
 

@@ -42,6 +42,37 @@ def test_batch_matches_single_and_exact_solutions(pc, graph):
             assert rel(host(u), ud) <= 1e-8
 
 
+@pytest.mark.parametrize("graph", [0, 1])
+@pytest.mark.parametrize("newton_steps", [1, 2])
+def test_batch_power_rule_matches_single(graph, newton_steps):
+    """The Sec. 2 stopping rule of the power method (at most 30 iterations, stop
+    when successive estimates differ by less than 1e-2 relative) applied per
+    instance and level in the lock-step batch: after the first Newton step
+    (random start) and the second (warm start) every estimate equals the one of
+    the instance's own single-problem solve.  The solves stop after
+    `newton_steps` steps, so a count that differs near the tolerance cannot
+    hide the comparison."""
+    specs = [(32, 5.0), (64, 2.0), (16, 6.3), (128, 3.3)]
+    o = jf().default_options(rtol_newton=1e-14, pc_dtype=jf().F64, eps_mode_pc=jf().EPS_PAPER, use_graph=graph,
+                             power_iters=30, power_tol=1e-2, max_newton=newton_steps)
+    ps = [jf().Problem("bratu2d", n, _levels(n), lam=lam, options=o) for n, lam in specs]
+    us = [torch.zeros((n + 1, n + 1), dtype=torch.float64, device="cuda") for n, _ in specs]
+    stats = jf().solve_batched(ps, us, o, check=False)
+    for (n, lam), u, st in zip(specs, us, stats):
+        q = jf().Problem("bratu2d", n, _levels(n), lam=lam, options=o)
+        u1 = torch.zeros_like(u)
+        st1 = q.solve(u1, check=False)
+        L = _levels(n)
+        assert st["newton_its"] == st1["newton_its"] == newton_steps
+        # the batched and the single-problem FD actions round differently (the
+        # estimates agree to ~1e-7); one iteration more or less would move an
+        # estimate by up to the rule's 1e-2
+        np.testing.assert_allclose(st["lambda_max"][1:L], st1["lambda_max"][1:L], rtol=1e-6)
+        # iterates of inexact Newton steps: the two FGMRES runs stop at the same
+        # forcing term but round differently (3e-8 measured after two steps)
+        assert rel(host(u), host(u1)) <= 1e-6
+
+
 def test_batch_of_64_uneven_instances():
     """The 64-instance batch workload: 64 instances, sizes from {129^2, 257^2, 513^2} nodes,
     lambda ~ U[1, 6.5] (seeded), FP32 preconditioner, FP64 outer, 1e-8."""

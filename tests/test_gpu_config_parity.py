@@ -33,7 +33,8 @@ def _gpu_nd(n, levels, pc):
     m = jf()
     o = m.default_options(nu_pre=2, nu_post=2, cheb_degree=4, rtol_newton=1e-8,
                           pc_dtype=m.F32 if pc == "f32" else m.F64,
-                          eps_mode_pc=m.EPS_FP32 if pc == "f32" else m.EPS_PAPER)
+                          eps_mode_pc=m.EPS_FP32 if pc == "f32" else m.EPS_PAPER,
+                          power_iters=30, power_tol=1e-2)  # the power method's Sec. 2 rule
     p = m.Problem("nd3d", n, levels, options=o)
     u = torch.zeros((n + 1,) * 3, dtype=torch.float64, device="cuda")
     st = p.solve(u)

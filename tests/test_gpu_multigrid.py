@@ -65,7 +65,7 @@ def test_transfers_parity(d, n, dt):
 
 
 @functools.lru_cache(maxsize=None)
-def _oracle_setup(kind, n, levels, pc, seed, lam, nu_pre, nu_post, cheb_degree, power_iters):
+def _oracle_setup(kind, n, levels, pc, seed, lam, nu_pre, nu_post, cheb_degree, power_iters, power_tol=0.0):
     """The oracle hierarchy after set-up at the seeded state (shared by the tests
     and kernel paths that use the same case; tests only read it, or set the
     fields they use before using them)."""
@@ -75,7 +75,7 @@ def _oracle_setup(kind, n, levels, pc, seed, lam, nu_pre, nu_post, cheb_degree, 
     load = fem.mms_load(n) if kind == "nd3d" else None
     lv = jfnk.build_hierarchy(kind, n, levels, lam=lam, load=load)
     oo = jfnk.Options(nu_pre=nu_pre, nu_post=nu_post, cheb_degree=cheb_degree, power_iters=power_iters,
-                      eps_mode_pc="fp32" if pc == "f32" else "paper", seed=seed)
+                      power_tol=power_tol, eps_mode_pc="fp32" if pc == "f32" else "paper", seed=seed)
     jfnk.setup_levels(lv, u, oo, 0)
     return lv, oo, u, tuple(x.lam_max for x in lv)
 
@@ -87,7 +87,7 @@ def _setup_pair(kind, n, levels, pc="f64", seed=0, lam=5.0, **kw):
               eps_mode_pc=jf().EPS_FP32 if pc == "f32" else jf().EPS_PAPER, seed=seed, **kw)
     p = jf().Problem(kind, n, levels, lam=lam, options=o)
     lv, oo, u, lam0 = _oracle_setup(kind, n, levels, pc, seed, lam, o.nu_pre, o.nu_post, o.cheb_degree,
-                                    o.power_iters)
+                                    o.power_iters, o.power_tol)
     for x, lm in zip(lv, lam0):  # a test may have set the GPU's estimates
         x.lam_max = lm
     p.mg_setup(dev(u), 0)
@@ -95,8 +95,13 @@ def _setup_pair(kind, n, levels, pc="f64", seed=0, lam=5.0, **kw):
 
 
 @pytest.mark.parametrize("kind,n,levels", [("bratu2d", 64, 4), ("nd3d", 32, 4)])
-def test_setup_projection_operator_and_power_method(kind, n, levels):
-    p, o, lv, oo, u = _setup_pair(kind, n, levels)
+@pytest.mark.parametrize("power", [(10, 0.0), (30, 1e-2)], ids=["fixed10", "rule"])
+def test_setup_projection_operator_and_power_method(kind, n, levels, power):
+    """Projection, A(x_l), the x statistics and the power method on every level.
+    power: a fixed count, or the Sec. 2 rule (at most 30 iterations, stop when
+    successive estimates differ by less than 1e-2 relative), where the library
+    checks every level's estimate after each round of iterations."""
+    p, o, lv, oo, u = _setup_pair(kind, n, levels, power_iters=power[0], power_tol=power[1])
     for l in range(levels):
         x = host(p.level_vector(l, "x"))
         assert rel(x, lv[l].x) <= 1e-14
@@ -107,7 +112,7 @@ def test_setup_projection_operator_and_power_method(kind, n, levels):
         m = lv[l].mask
         assert info["sum_abs_x"] == pytest.approx(np.abs(lv[l].x[m]).sum(), rel=1e-12)
         if l >= 1:
-            # same SplitMix64 start vector, 10 FD power iterations on both sides
+            # same SplitMix64 start vector, the same FD power iterations on both sides
             assert info["lambda_max"] == pytest.approx(lv[l].lam_max, rel=1e-6), l
             # the eigenvector estimate is a direction: the library keeps the last
             # action's output J v/||v||, the oracle the normalised vector
