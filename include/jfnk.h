@@ -167,7 +167,12 @@ void jfnk_paper_options(jfnk_options* opts);
  *                               1024; < 0: that kernel is not used)
  *   JFNK_V3_F32                 FP32 halo-free levels: 0 one element a thread,
  *                               1 / 2 two elements a thread with one / two CTAs
- *                               per SM, 3 (default) two, CTAs chosen per mode */
+ *                               per SM, 3 (default) two, CTAs chosen per mode
+ *   JFNK_ZM3D_MIN_N_F64 / _F32  element-parallel levels with n >= this (> 0)
+ *                               march element columns along z (default 0: no)
+ *   JFNK_EP3D_CLUSTER_MIN_N / _MAX_N  FP32 element-parallel levels with n in
+ *                               this range (at most 32) run in one thread-block
+ *                               cluster (defaults 16 / 16; _MAX_N 0: never) */
 jfnk_status jfnk_problem_create(const jfnk_problem_desc* desc, jfnk_problem** out);
 jfnk_status jfnk_problem_destroy(jfnk_problem* p);
 

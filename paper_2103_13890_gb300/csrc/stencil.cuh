@@ -83,6 +83,8 @@ struct StencilArgs {
     long long face_cap;
     int ep_max_n;
     int zm_min_n;        // element-parallel levels with n >= zm_min_n (> 0) march element columns along z
+    int cl_min_n, cl_max_n;  // FP32 element-parallel levels with cl_min_n <= n <= cl_max_n run in one
+                             // thread-block cluster (stencil_ep.cu; cl_max_n 0: never)
     int v2_threads;      // cap on the CTA size of the halo-free kernel (0: 1024; < 0: not used)
     int v3;              // FP32: the halo-free kernel's two-elements-per-thread variant (0: not used;
                          // 1 / 2: one / two CTAs per SM; other: chosen per mode)

@@ -15,6 +15,9 @@
 // kernels (bound by the FP64 pipe by two orders of magnitude) do not notice
 // and which stays in L2 on the small levels.
 #include <algorithm>
+#include <atomic>
+
+#include <cooperative_groups.h>
 
 #include "element.cuh"
 #include "reduce.cuh"
@@ -382,6 +385,182 @@ __global__ void __launch_bounds__(kEpSmallThreads) ep3d_small_kernel(const Stenc
     }
 }
 
+// FP32 levels with n <= kEpClusterMaxN: the level in one thread-block
+// cluster of up to 16 CTAs, the contributions in distributed shared memory.
+// CTA r of the cluster owns element slices z in [r S, r S + S) (S = ceil(n /
+// 16)) and the node planes with the same z (the last CTA also plane n).  A
+// node plane takes its lower-z elements' contributions from the CTA below
+// through DSMEM after a cluster barrier; the norm is summed over the CTAs' block
+// sums in rank order.  One launch and no round trip through global memory or a
+// completion counter, for levels whose two-launch form is a chain of
+// latencies.  The element values and the per-node sums (same order) are those
+// of the element-parallel pair.
+constexpr int kEpClusterThreads = 1024;
+constexpr int kEpClusterMaxCtas = 16;
+constexpr int kEpClusterMaxN = 32;  // S <= 2: 8 S n^2 words = 64 KB of shared memory at n = 32
+
+__host__ __device__ inline int ep3d_cluster_slices(int n) { return (n + kEpClusterMaxCtas - 1) / kEpClusterMaxCtas; }
+__host__ __device__ inline int ep3d_cluster_ctas(int n) {
+    const int S = ep3d_cluster_slices(n);
+    return (n + S - 1) / S;
+}
+
+template <typename T, Prob P, Mode M>
+__global__ void __launch_bounds__(kEpClusterThreads) ep3d_cluster_kernel(const StencilArgs<T> a) {
+    namespace cg = cooperative_groups;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* Cs = reinterpret_cast<T*>(smem_raw);  // [8][S][n][n]: this CTA's element contributions
+    __shared__ double red_sm[32];
+    __shared__ double bsums[kEpClusterMaxCtas];  // rank 0: every CTA's block sum
+    cg::cluster_group cluster = cg::this_cluster();
+    const int rank = (int)cluster.block_rank();
+    const int ncta = (int)cluster.num_blocks();
+    const int n = a.g.n, NP = n + 1, nn = n * n;
+    const int S = ep3d_cluster_slices(n);
+    const int E = S * nn;  // stride of a corner in every CTA's array
+    const int z0 = rank * S;
+    const int z1 = min(z0 + S, n);
+    const int sy = (int)a.g.sy, sz = (int)a.g.sz;
+    T eps = T(0);
+    if (M != Mode::F) eps = eps_of<T>(a.eps);
+    for (int e = threadIdx.x; e < (z1 - z0) * nn; e += blockDim.x) {
+        const int x = e % n, y = (e / n) % n, z = z0 + e / nn;
+        T ue[8];
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            const int X = x + (c & 1), Y = y + ((c >> 1) & 1), Z = z + (c >> 2);
+            const int idx = (int)JFNK_IDX(Z * sz + Y * sy + X, a.g.size);
+            const bool bnd = X == 0 || X == n || Y == 0 || Y == n || Z == 0 || Z == n;
+            T uv = a.u[idx];
+            if (M != Mode::F && !bnd) uv += eps * a.v[idx];
+            ue[c] = uv;
+        }
+        T r[8];
+        if (P == Prob::NDK3)
+            elem_nd3<T, true>(ue, a.kappa[JFNK_IDX(z * nn + y * n + x, (long long)nn * n)], r);
+        else
+            elem_nd3<T, false>(ue, T(1), r);
+#pragma unroll
+        for (int c = 0; c < 8; ++c) Cs[c * E + e] = r[c];
+    }
+    cluster.sync();
+    // the CTA below holds slice z0 - 1, its last (S is full for every CTA but the last)
+    const T* Cd = rank > 0 ? cluster.map_shared_rank(Cs, rank - 1) : Cs;
+    T inv_eps = T(0);
+    if (M != Mode::F) inv_eps = inv_eps_of<T>(a.eps);
+    ChebK<T> ck = {T(0), T(0), T(0)};
+    if (M == Mode::CHEB0 || M == Mode::CHEB || M == Mode::CHEBLAST) ck = cheb_of<T>(a.cheb, a.cheb_step);
+    float red = 0.f;
+    const int zend = (rank == ncta - 1) ? NP : z1;
+    for (int i = threadIdx.x; i < (zend - z0) * NP * NP; i += blockDim.x) {
+        const int X = i % NP, YZ = i / NP;
+        const int Y = YZ % NP, Z = z0 + YZ / NP;
+        const bool inner = X > 0 && X < n && Y > 0 && Y < n && Z > 0 && Z < n;
+        T val = T(0);
+        if (inner) {
+            // corner c of element (X - dx, Y - dy, Z - dz), c = dx + 2 dy + 4 dz
+            const int e0 = (int)JFNK_IDX((Z - z0) * nn + Y * n + X, E);  // element (X, Y, Z), this CTA
+            const T c0 = Cs[e0], c1 = Cs[E + e0 - 1];
+            const T c2 = Cs[2 * E + e0 - n], c3 = Cs[3 * E + e0 - n - 1];
+            const T* Cl = (Z > z0) ? Cs : Cd;                            // slice Z - 1
+            const int e1 = (int)JFNK_IDX(((Z > z0) ? (Z - 1 - z0) : (S - 1)) * nn + Y * n + X, E);
+            const T c4 = Cl[4 * E + e1], c5 = Cl[5 * E + e1 - 1];
+            const T c6 = Cl[6 * E + e1 - n], c7 = Cl[7 * E + e1 - n - 1];
+            val = (((c0 + c1) + (c2 + c3)) + ((c4 + c5) + (c6 + c7))) * a.node_scale;
+        }
+        epilogue<T, M>(a, (int)JFNK_IDX(Z * sz + Y * sy + X, a.g.size), inner, val, inv_eps, ck, red);
+    }
+    if (a.red != RedOut::NONE) {
+        const double bs = block_sum(red, red_sm);
+        if (threadIdx.x == 0) *cluster.map_shared_rank(&bsums[rank], 0) = bs;
+    }
+    // every CTA is done with its neighbour's contributions and has posted its
+    // block sum to rank 0; after this barrier no CTA touches another's memory
+    cluster.sync();
+    if (a.red != RedOut::NONE && rank == 0 && threadIdx.x == 0) {
+        double tot = 0.0;
+        for (int q = 0; q < ncta; ++q) tot += bsums[q];
+        const double nrm = sqrt(tot);
+        if (a.red_norm) *a.red_norm = nrm;
+        if (a.red == RedOut::EPS || a.red == RedOut::EPS_UNIT)
+            set_eps_slot(a.red_eps, a.epsp, nrm, a.red == RedOut::EPS_UNIT, a.status);
+    }
+}
+
+template <Prob P, Mode M>
+static cudaError_t ep3d_cluster_attrs() {
+    auto k = ep3d_cluster_kernel<float, P, M>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)(8 * 2 * kEpClusterMaxN * kEpClusterMaxN * sizeof(float)));
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    return e;
+}
+
+template <Prob P>
+static cudaError_t ep3d_cluster_attrs_p() {
+    cudaError_t e = ep3d_cluster_attrs<P, Mode::F>();
+    if (e == cudaSuccess) e = ep3d_cluster_attrs<P, Mode::JV>();
+    if (e == cudaSuccess) e = ep3d_cluster_attrs<P, Mode::BMJ>();
+    if (e == cudaSuccess) e = ep3d_cluster_attrs<P, Mode::CHEB0>();
+    if (e == cudaSuccess) e = ep3d_cluster_attrs<P, Mode::CHEB>();
+    if (e == cudaSuccess) e = ep3d_cluster_attrs<P, Mode::CHEBLAST>();
+    return e;
+}
+
+bool ep3d_cluster_init() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return false;
+    static std::atomic<int> ok[64];  // per device: 0 unknown, 1 usable, -1 not
+    if (dev < 0 || dev >= 64) return false;
+    if (ok[dev].load() != 0) return ok[dev].load() > 0;
+    cudaError_t e = ep3d_cluster_attrs_p<Prob::ND3>();
+    if (e == cudaSuccess) e = ep3d_cluster_attrs_p<Prob::NDK3>();
+    int clusters = 0;
+    if (e == cudaSuccess) {
+        // the largest launch (n = kEpClusterMaxN) must fit on the device
+        cudaLaunchConfig_t cfg = {};
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = ep3d_cluster_ctas(kEpClusterMaxN);
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.gridDim = dim3(ep3d_cluster_ctas(kEpClusterMaxN));
+        cfg.blockDim = dim3(kEpClusterThreads);
+        cfg.dynamicSmemBytes = 8 * 2 * kEpClusterMaxN * kEpClusterMaxN * sizeof(float);
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        e = cudaOccupancyMaxActiveClusters(&clusters, ep3d_cluster_kernel<float, Prob::ND3, Mode::CHEB>, &cfg);
+    }
+    if (e != cudaSuccess) cudaGetLastError();  // clear: the pair of kernels runs instead
+    ok[dev].store((e == cudaSuccess && clusters > 0) ? 1 : -1);
+    return ok[dev].load() > 0;
+}
+
+template <typename T, Prob P, Mode M>
+static jfnk_status launch_ep3d_cluster(const StencilArgs<T>& a, cudaStream_t st) {
+    const int n = a.g.n;
+    const int ncta = ep3d_cluster_ctas(n);
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = ncta;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(ncta);
+    cfg.blockDim = dim3(kEpClusterThreads);
+    cfg.dynamicSmemBytes = 8ull * ep3d_cluster_slices(n) * n * n * sizeof(T);
+    cfg.stream = st;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    const cudaError_t e = cudaLaunchKernelEx(&cfg, ep3d_cluster_kernel<T, P, M>, a);
+    if (e != cudaSuccess) {
+        set_error("cluster launch: %s", cudaGetErrorString(e));
+        return JFNK_ERR_CUDA;
+    }
+    JFNK_LAUNCH_CHECK();
+    return JFNK_OK;
+}
+
 template <typename T, Prob P, Mode M, bool ADJ>
 static jfnk_status launch_ep3d_pm(const StencilArgs<T>& a, cudaStream_t st) {
     const Grid& g = a.g;
@@ -393,6 +572,10 @@ static jfnk_status launch_ep3d_pm(const StencilArgs<T>& a, cudaStream_t st) {
     if (g.n > 1024) {
         set_error("element-parallel kernels: n = %d beyond 1024 (32-bit node indices, grid rows)", g.n);
         return JFNK_ERR_INVALID_ARG;
+    }
+    if constexpr (sizeof(T) == 4 && !ADJ) {
+        if (g.n >= a.cl_min_n && g.n <= std::min(a.cl_max_n, kEpClusterMaxN) && ep3d_cluster_init())
+            return launch_ep3d_cluster<T, P, M>(a, st);
     }
     if (sizeof(T) == 4 && (long long)g.n * g.n * g.n <= kEpSmallElems) {
         ep3d_small_kernel<T, P, M, ADJ><<<1, kEpSmallThreads, 0, st>>>(a);

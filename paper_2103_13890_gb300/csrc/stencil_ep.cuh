@@ -33,6 +33,11 @@ inline bool ep3d_use(const StencilArgs<T>& a, bool adj = false) {
            ep3d_scratch_need(a.g, zm) <= a.face_cap;
 }
 
+// Sets the cluster kernels' attributes on the current device (once) and
+// returns whether a cluster of their largest size fits there.  Called by the
+// launcher; callers that capture launches into a graph call it first.
+bool ep3d_cluster_init();
+
 // adj: the vector-Jacobian product (J^T v, and (dF/dkappa)^T v into a.dkout)
 // in place of the FD action.
 template <typename T>

@@ -20,12 +20,14 @@ PATHS = {
            "JFNK_ZM3D_MIN_N_F32": "2"},
     "tiled": {"JFNK_EP3D_MAX_N_F64": "0", "JFNK_EP3D_MAX_N_F32": "0"},
     "v2": {"JFNK_EP3D_MAX_N_F64": "0", "JFNK_EP3D_MAX_N_F32": "0", "JFNK_V3_F32": "0"},
+    "cluster": {"JFNK_EP3D_MAX_N_F64": "100000", "JFNK_EP3D_MAX_N_F32": "100000", "JFNK_ZM3D_MIN_N_F64": "0",
+                "JFNK_EP3D_CLUSTER_MIN_N": "2", "JFNK_EP3D_CLUSTER_MAX_N": "32"},
 }
 
 
 def set_path(name):
     for k in ("JFNK_EP3D_MAX_N_F64", "JFNK_EP3D_MAX_N_F32", "JFNK_ZM3D_MIN_N_F64", "JFNK_ZM3D_MIN_N_F32",
-              "JFNK_V3_F32"):
+              "JFNK_V3_F32", "JFNK_EP3D_CLUSTER_MIN_N", "JFNK_EP3D_CLUSTER_MAX_N"):
         os.environ.pop(k, None)
     os.environ.update(PATHS[name])
 

@@ -37,9 +37,13 @@ def rel(a, b):
 KERNEL_PATHS = {
     "default": {},
     "ep": {"JFNK_EP3D_MAX_N_F64": "100000", "JFNK_EP3D_MAX_N_F32": "100000", "JFNK_ZM3D_MIN_N_F64": "0",
-           "JFNK_ZM3D_MIN_N_F32": "0"},
+           "JFNK_ZM3D_MIN_N_F32": "0", "JFNK_EP3D_CLUSTER_MAX_N": "0"},
     "zm": {"JFNK_EP3D_MAX_N_F64": "100000", "JFNK_EP3D_MAX_N_F32": "100000", "JFNK_ZM3D_MIN_N_F64": "2",
-           "JFNK_ZM3D_MIN_N_F32": "2"},
+           "JFNK_ZM3D_MIN_N_F32": "2", "JFNK_EP3D_CLUSTER_MAX_N": "0"},
+    # FP32 element-parallel levels with n <= 32 in one thread-block cluster
+    # (the FP64 levels as on "ep")
+    "cluster": {"JFNK_EP3D_MAX_N_F64": "100000", "JFNK_EP3D_MAX_N_F32": "100000", "JFNK_ZM3D_MIN_N_F64": "0",
+                "JFNK_ZM3D_MIN_N_F32": "0", "JFNK_EP3D_CLUSTER_MIN_N": "2", "JFNK_EP3D_CLUSTER_MAX_N": "32"},
     "tiled": {"JFNK_EP3D_MAX_N_F64": "0", "JFNK_EP3D_MAX_N_F32": "0"},
     "v2": {"JFNK_EP3D_MAX_N_F64": "0", "JFNK_EP3D_MAX_N_F32": "0", "JFNK_V3_F32": "0"},
     # the two-elements-per-thread kernel with one / two CTAs per SM in every
@@ -51,7 +55,7 @@ KERNEL_PATHS = {
 
 def kernel_path(monkeypatch, path):
     for k in ("JFNK_EP3D_MAX_N_F64", "JFNK_EP3D_MAX_N_F32", "JFNK_V3_F32", "JFNK_ZM3D_MIN_N_F64",
-              "JFNK_ZM3D_MIN_N_F32"):
+              "JFNK_ZM3D_MIN_N_F32", "JFNK_EP3D_CLUSTER_MIN_N", "JFNK_EP3D_CLUSTER_MAX_N"):
         monkeypatch.delenv(k, raising=False)
     for k, v in KERNEL_PATHS[path].items():
         monkeypatch.setenv(k, v)

@@ -142,15 +142,16 @@ def test_chebyshev_smoother_parity(kind, n, levels, path, nu, zero, monkeypatch)
     assert rel(host(s), so) <= _fd_tol(so, se)
 
 
-@pytest.mark.parametrize("path", ["default", "tiled", "v2", "v3two", "ep", "zm"])
-def test_chebyshev_smoother_fp32_3d(path, monkeypatch):
-    """FP32 smoothing on the finest level of a 65^3 hierarchy (on the "tiled"
-    path the two-elements-per-thread halo-free kernel, on "v2" the one-element
-    kernel, on "ep"/"default" the element-parallel kernels): every fused
-    Chebyshev mode against the oracle's FP64 smoother to FP32-FD accuracy, and
-    the FP32 kernels against each other to the FP32 FD round-off."""
+@pytest.mark.parametrize("n,levels,path", [(64, 5, p) for p in ("default", "tiled", "v2", "v3two", "ep", "zm")]
+                         + [(32, 4, p) for p in ("default", "ep", "zm", "cluster")])
+def test_chebyshev_smoother_fp32_3d(n, levels, path, monkeypatch):
+    """FP32 smoothing on the finest level of a 65^3 / 33^3 hierarchy (on the
+    "tiled" path the two-elements-per-thread halo-free kernel, on "v2" the
+    one-element kernel, on "ep"/"default" the element-parallel kernels, on
+    "cluster" the one-cluster kernel): every fused Chebyshev mode against the
+    oracle's FP64 smoother to FP32-FD accuracy, and the FP32 kernels against
+    each other to the FP32 FD round-off."""
     kernel_path(monkeypatch, path)
-    n, levels = 64, 5
     p, o, lv, oo, u = _setup_pair("nd3d", n, levels, pc="f32")
     l = levels - 1
     b = random_direction(n, 3, seed=31) * 1e-3
@@ -163,7 +164,7 @@ def test_chebyshev_smoother_fp32_3d(path, monkeypatch):
         so = jfnk.chebyshev(lv[l], init.copy(), lv[l].x, lv[l].Fx, b, nu, o.cheb_degree, lam, o.cheb_lo,
                             o.cheb_hi, mode="fp32")
         assert rel(host(s), so) <= 1e-3
-        _FP32_SMOOTH.setdefault((zero, nu), {})[path] = host(s)
+        _FP32_SMOOTH.setdefault((n, zero, nu), {})[path] = host(s)
     # every path run so far in this session agrees to the FP32 FD round-off:
     # each action carries ~2^-23 / sqrt(2^-23) = 3.5e-4 relative noise of its own
     # rounding order, of which 1e-3 leaves room for a few actions
@@ -212,15 +213,16 @@ def test_vcycle_parity(kind, n, levels, path, monkeypatch):
     assert rel(s, so) <= _fd_tol(so, se, 1e-9)
 
 
+@pytest.mark.parametrize("kind,n,levels,path", [("bratu2d", 64, 4, "default"), ("nd3d", 32, 4, "ep"),
+                                                ("nd3d", 32, 4, "cluster")])
 @pytest.mark.parametrize("pc", ["f64", "f32"])
-def test_vcycle_fp32_parity_and_contraction(pc):
-    """The FP32 preconditioner agrees with the FP64 oracle to FP32 accuracy and
-    both contract the linearised error like a multigrid cycle."""
-    kind, n, levels = "bratu2d", 64, 4
+def test_vcycle_fp32_parity_and_contraction(pc, kind, n, levels, path, monkeypatch):
+    """The FP32 preconditioner agrees with the FP64 oracle to FP32 accuracy."""
+    kernel_path(monkeypatch, path)
     p, o, lv, oo, u = _setup_pair(kind, n, levels, pc=pc)
     for l in range(1, levels):
         lv[l].lam_max = p.level_info(l)["lambda_max"]
-    b = random_direction(n, 2, seed=61)
+    b = random_direction(n, fem.dim_of(kind), seed=61)
     bd = dev(b, torch.float64)
     s = host(p.mg_vcycle(bd))
     so = jfnk.mg_vcycle(lv, levels - 1, b, oo)
@@ -249,7 +251,7 @@ def _nd_direct_solution(n):
 
 
 @pytest.mark.parametrize("pc,path", [("f64", "default"), ("f32", "default"), ("f64", "tiled"), ("f32", "ep"),
-                                     ("f64", "zm"), ("f32", "zm")])
+                                     ("f64", "zm"), ("f32", "zm"), ("f32", "cluster")])
 def test_solve_nd_matches_discrete_solution(pc, path, monkeypatch):
     kernel_path(monkeypatch, path)
     n = 24  # 25^3 nodes, 4 levels down to 3^3 elements (a sparse direct solve at this size is quick)
@@ -264,10 +266,12 @@ def test_solve_nd_matches_discrete_solution(pc, path, monkeypatch):
     assert rel(host(u), ud) <= 1e-8
 
 
-@pytest.mark.parametrize("kind,n,levels", [("bratu2d", 64, 4), ("nd3d", 32, 4)])
-def test_graph_replay_matches_direct_launches(kind, n, levels):
+@pytest.mark.parametrize("kind,n,levels,path", [("bratu2d", 64, 4, "default"), ("nd3d", 32, 4, "default"),
+                                                ("nd3d", 32, 4, "cluster")])
+def test_graph_replay_matches_direct_launches(kind, n, levels, path, monkeypatch):
     """The V-cycle replayed from a captured CUDA graph runs the same kernels on
     the same device scalars: the solve is bit-identical to direct launches."""
+    kernel_path(monkeypatch, path)
     d = fem.dim_of(kind)
     sols, stats = [], []
     for g in (0, 1):

@@ -51,6 +51,11 @@ PATH_CASES = [(k, n, path) for k, n in CASES for path in ("default", "ep", "zm",
 PATH_CASES += [(k, n, path) for k, n in CASES for path in ("v2", "v3one")
                if k != "bratu2d" and n % 32 == 0 and n >= 64]
 PATH_CASES += [("nd3d", 128, "default")]
+# FP32 levels in one thread-block cluster: whole slices a CTA (n = 4, 16), two
+# slices a CTA (32), a ragged last CTA (n = 5: 5 CTAs; 13; 27: 14 CTAs, the last
+# with one slice)
+PATH_CASES += [(k, n, "cluster") for k, n in (("nd3d", 4), ("ndk3d", 5), ("ndk3d", 13), ("nd3d", 16),
+                                               ("nd3d", 27), ("nd3d", 32))]
 
 
 @functools.lru_cache(maxsize=None)
@@ -144,7 +149,9 @@ def test_jvp_fp64_parity(kind, n, path, monkeypatch):
 @pytest.mark.parametrize("kind,n,path", [("bratu2d", 64, "default"), ("nd3d", 33, "default"),
                                          ("nd3d", 33, "tiled"), ("nd3d", 33, "zm"), ("nd3d", 64, "default"),
                                          ("nd3d", 64, "ep"),
-                                         ("nd3d", 64, "tiled"), ("nd3d", 64, "v2"), ("nd3d", 96, "default")])
+                                         ("nd3d", 64, "tiled"), ("nd3d", 64, "v2"), ("nd3d", 96, "default"),
+                                         ("nd3d", 16, "cluster"), ("nd3d", 27, "cluster"),
+                                         ("nd3d", 32, "cluster")])
 def test_jvp_fp32_parity(kind, n, path, monkeypatch):
     """FP32 action with the single-precision step eps = sqrt(2^-23)(1+||u||)/||v||
     against the oracle's FP64 evaluation of the same quotient."""
