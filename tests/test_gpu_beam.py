@@ -7,6 +7,7 @@ import numpy as np
 import pytest
 
 from gpu_common import dev, host, jf, rel, torch
+from golden import make_beam_cg_envelope
 from oracle import hyper, jfnk
 
 pytestmark = pytest.mark.gpu
@@ -170,3 +171,39 @@ def test_vcycle_near_the_solution_is_finite_and_of_the_oracles_size():
             rhs = b if j == 0 else b * (1.0 + 1e-13 * np.random.default_rng(100 + j).normal(size=b.shape))
             norms.append(np.linalg.norm(jfnk.mg_vcycle(lvs, k, rhs, oo)))
         assert 0.1 * min(norms) <= np.linalg.norm(s) <= 10.0 * max(norms), (np.linalg.norm(s), norms)
+
+
+@pytest.mark.parametrize("k", [1, 2])
+def test_paper_solver_counts_within_the_oracles_envelope(k):
+    """Bound on the beam's cost.  The shifted coarse CG of Alg. 1 makes the
+    outer CG counts scatter with rounding: the oracle's own totals over 17
+    starts that differ by 1e-13 range over 40-417 (L1) and 22-446 (L2)
+    (tests/golden/beam_cg_envelope.txt).  From the same 17 starts the GPU must
+    (i) converge with Newton counts inside the oracle's range +- 1, (ii) repeat
+    the oracle's CG counts exactly on the leading Newton steps where every
+    oracle run agrees, (iii) stay at or under max_linear in every step, and
+    (iv) have a median total of at most 5x the oracle's median (a run of the
+    same distribution fails this with probability below 1e-3, a systematic
+    blow-up does not pass it)."""
+    env = make_beam_cg_envelope.load()[k]
+    runs = sorted(env)
+    o = jf().paper_options()
+    p = jf().Problem("beam3d", 2 ** k, k + 1, options=o)
+    newton_o = [r[1] for r in runs]
+    totals_o = sorted(r[2] for r in runs)
+    hists_o = [r[3] for r in runs]
+    lead = 0
+    while all(len(h) > lead for h in hists_o) and len({h[lead] for h in hists_o}) == 1:
+        lead += 1
+    assert lead >= 3
+    totals = []
+    for run, _, _, _ in runs:
+        u = dev(make_beam_cg_envelope.initial_state(k, run))
+        st = p.solve(u)
+        assert st["converged"], (run, st)
+        assert min(newton_o) - 1 <= st["newton_its"] <= max(newton_o) + 1, (run, st["newton_its"])
+        assert st["lin_hist"][:lead] == hists_o[0][:lead], (run, st["lin_hist"])
+        assert max(st["lin_hist"]) <= o.max_linear
+        totals.append(st["linear_its"])
+    print(f"L{k} CG totals, GPU: {sorted(totals)}; oracle: {totals_o}")
+    assert np.median(totals) <= 5 * np.median(totals_o), (sorted(totals), totals_o)
