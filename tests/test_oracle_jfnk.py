@@ -240,3 +240,50 @@ def test_splitmix_counter_form_equals_sequential_stream():
     v = splitmix.uniform_pm1(7, 2, np.arange(200000, dtype=np.uint64))
     assert -1.0 <= v.min() and v.max() < 1.0
     assert abs(v.mean()) < 0.01 and abs(v.var() - 1.0 / 3.0) < 0.01
+
+
+def test_power_method_stopping_rule_on_two_eigenmodes():
+    """The Sec. 2 stopping rule (stop once successive estimates differ by less
+    than tol, read relative to the newer one, after at least two iterations).
+    Linear limit x = 0, J = K, start vector alpha e_A + beta e_B of two
+    orthonormal sine eigenvectors: the k-th estimate is
+    sqrt(a^2 mu_A^2k + b^2 mu_B^2k) / sqrt(a^2 mu_A^2(k-1) + b^2 mu_B^2(k-1)),
+    so the iteration where the rule stops, and the estimate it returns, follow
+    in closed form."""
+    n = 8
+    h = 1.0 / n
+    lv = jfnk.Level("nd3d", n, 0.0, None, None)
+    x = np.zeros((n + 1,) * 3)
+    Fx = lv.F(x)
+    s, c = _eig_1d(n)
+
+    def mu(i, j, k):
+        return 4 * h / 9 * (s[i - 1] * c[j - 1] * c[k - 1] + c[i - 1] * s[j - 1] * c[k - 1]
+                            + c[i - 1] * c[j - 1] * s[k - 1])
+
+    mA, mB = (3, 2, 1), (1, 2, 1)
+    muA, muB = mu(*mA), mu(*mB)
+    eA, eB = _sine_mode(n, 3, mA), _sine_mode(n, 3, mB)
+    eA, eB = eA / np.linalg.norm(eA), eB / np.linalg.norm(eB)
+    assert abs(np.vdot(eA, eB)) < 1e-14
+    # the modes are eigenvectors of the linearised operator
+    for e, m in ((eA, muA), (eB, muB)):
+        Je = jfnk.fd_jv(lv, x, Fx, e)
+        assert np.linalg.norm(Je - m * e) <= 1e-7 * m
+    al, be = 0.3, 1.0
+    lam = [np.sqrt(al ** 2 * muA ** (2 * k) + be ** 2 * muB ** (2 * k))
+           / np.sqrt(al ** 2 * muA ** (2 * k - 2) + be ** 2 * muB ** (2 * k - 2)) for k in range(1, 40)]
+    stops = []
+    for tol in (1e-2, 1e-3, 1e-4):
+        K = next(k for k in range(1, len(lam)) if abs(lam[k] - lam[k - 1]) < tol * lam[k])
+        stops.append(K)
+        # the closed-form sequence decides the stop with a clear margin
+        assert abs(lam[K] - lam[K - 1]) < 0.95 * tol * lam[K]
+        assert K < 2 or abs(lam[K - 1] - lam[K - 2]) > 1.05 * tol * lam[K - 1]
+        got, _ = jfnk.power_method(lv, x, Fx, al * eA + be * eB, 30, tol=tol)
+        assert got == pytest.approx(lam[K], rel=1e-7)
+        assert abs(lam[K] - lam[K + 1]) > 100 * 1e-7 * lam[K] and abs(lam[K] - lam[K - 1]) > 100 * 1e-7 * lam[K]
+    assert stops[0] < stops[1] < stops[2] < 29
+    # the iteration cap wins over the rule
+    got, _ = jfnk.power_method(lv, x, Fx, al * eA + be * eB, 2, tol=1e-12)
+    assert got == pytest.approx(lam[1], rel=1e-7)
