@@ -20,6 +20,7 @@
 // epilogue.  The fixup kernel also completes the norm reduction, so results are
 // deterministic.  Every F_i is still the sum of the same element integrals.
 #include <algorithm>
+#include <atomic>
 #include <cstdio>
 
 #include "element.cuh"
@@ -32,6 +33,15 @@
 #define JFNK_IDX_FACE(i) JFNK_IDX((i), a.face_cap)
 
 namespace jfnk {
+
+// Bit of the current device in a per-kernel mask of devices whose function
+// attributes are set (function attributes are set per device).  Ordinals from
+// 63 up get no bit and set the attributes at every launch.
+static unsigned long long device_bit() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 63) return 0;
+    return 1ull << dev;
+}
 
 template <typename T>
 __device__ __forceinline__ T eps_of2(const EpsSlot* s);
@@ -743,11 +753,12 @@ static jfnk_status launch_v2_pm(const StencilArgs<T>& a, cudaStream_t st) {
         return JFNK_ERR_INVALID_ARG;
     }
     const size_t smem = sizeof(T) * (3 * (size_t)(q.BY + 1) * (q.n + 1) + 16 * (size_t)q.BY * q.n);
-    static bool attr_set = false;
-    if (!attr_set) {
+    static std::atomic<unsigned long long> attr_devs{0};  // devices whose attribute is set
+    const unsigned long long dbit = device_bit();
+    if (!(attr_devs.load() & dbit)) {
         JFNK_CUDA_TRY(cudaFuncSetAttribute(stencil3d_v2_kernel<T, P, M>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            220 * 1024));
-        attr_set = true;
+        attr_devs.fetch_or(dbit);
     }
     stencil3d_v2_kernel<T, P, M><<<dim3(q.Ty, q.Tz), dim3(q.n, q.BY), smem, st>>>(a, q);
     JFNK_LAUNCH_CHECK();
@@ -781,13 +792,14 @@ static jfnk_status launch_v3_pmb(const StencilArgs<float>& a, cudaStream_t st) {
     }
     const size_t NP = (size_t)q.n + 2;
     const size_t smem = sizeof(float) * (3 * (size_t)(q.BY + 1) * NP + 16 * (size_t)q.BY * NP);
-    static bool attr_set = false;
-    if (!attr_set) {
+    static std::atomic<unsigned long long> attr_devs{0};  // devices whose attributes are set
+    const unsigned long long dbit = device_bit();
+    if (!(attr_devs.load() & dbit)) {
         JFNK_CUDA_TRY(cudaFuncSetAttribute(stencil3d_v3_kernel<P, M, MINB>,
                                            cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024 / MINB));
         JFNK_CUDA_TRY(cudaFuncSetAttribute(stencil3d_v3_kernel<P, M, MINB>,
                                            cudaFuncAttributePreferredSharedMemoryCarveout, 100));
-        attr_set = true;
+        attr_devs.fetch_or(dbit);
     }
     stencil3d_v3_kernel<P, M, MINB><<<dim3(q.Ty, q.Tz), dim3(q.n / 2, q.BY), smem, st>>>(a, q);
     JFNK_LAUNCH_CHECK();
