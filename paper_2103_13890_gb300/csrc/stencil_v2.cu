@@ -419,43 +419,48 @@ __global__ void __launch_bounds__(kV3Threads, MINB) stencil3d_v3_kernel(const St
     ChebK2<float> ck = {0.f, 0.f, 0.f};
     if (M == Mode::CHEB0 || M == Mode::CHEB || M == Mode::CHEBLAST) ck = cheb_of2<float>(a.cheb, a.cheb_step);
 
-    auto node_val = [&](int x, int y, int z) -> float {
+    // u and the masked direction v (0 on the boundary) of node (x, y, z); w = u +
+    // eps v is formed when the plane is stored, so that no instruction waits on
+    // the loads before the layer's element arithmetic
+    auto node_uv = [&](int x, int y, int z, float& uu, float& vv) {
         const int idx = (int)JFNK_IDX(z * sz32 + y * sy32 + x, g.size);
-        float val = a.u[idx];
+        uu = a.u[idx];
+        vv = 0.f;
         if (M != Mode::F) {
             const bool bnd = x == 0 || x == n || y == 0 || y == n || z == 0 || z == n;
-            if (!bnd) val += eps * a.v[idx];
+            if (!bnd) vv = a.v[idx];
         }
-        return val;
     };
     // this thread's share of a plane: nodes (2t, 2t+1) of row y0+w, of row
     // y0+BY (w == 0), and node n of those rows (last t)
     const bool extra_row = (w == 0);
     const bool extra_col = (x0 == n - 2);
-    // the next plane in registers: loaded at the start of a layer, stored to
-    // the ring after the layer's element arithmetic
+    // the next plane in registers (u in p, v in q): loaded at the start of a
+    // layer, stored to the ring after the layer's element arithmetic
     float p0 = 0.f, p1 = 0.f, p2 = 0.f, p3 = 0.f, p4 = 0.f, p5 = 0.f;
-    auto load_plane = [&](int z, float& r0, float& r1, float& r2, float& r3, float& r4, float& r5) {
-        r0 = node_val(x0, y0 + w, z);
-        r1 = node_val(x0 + 1, y0 + w, z);
-        if (extra_col) r2 = node_val(n, y0 + w, z);
+    float q0 = 0.f, q1 = 0.f, q2 = 0.f, q3 = 0.f, q4 = 0.f, q5 = 0.f;
+    auto load_plane = [&](int z) {
+        node_uv(x0, y0 + w, z, p0, q0);
+        node_uv(x0 + 1, y0 + w, z, p1, q1);
+        if (extra_col) node_uv(n, y0 + w, z, p2, q2);
         if (extra_row) {
-            r3 = node_val(x0, y0 + BY, z);
-            r4 = node_val(x0 + 1, y0 + BY, z);
+            node_uv(x0, y0 + BY, z, p3, q3);
+            node_uv(x0 + 1, y0 + BY, z, p4, q4);
         }
-        if (extra_row && extra_col) r5 = node_val(n, y0 + BY, z);
+        if (extra_row && extra_col) node_uv(n, y0 + BY, z, p5, q5);
     };
+    auto wv = [&](float uu, float vv) { return M != Mode::F ? uu + eps * vv : uu; };
     auto store_plane = [&](int buf) {
         float* Wb = W + buf * (BY + 1) * NP;
-        pf2_store(Wb + w * NP + x0, pf2_pack(p0, p1));
-        if (extra_col) Wb[w * NP + n] = p2;
-        if (extra_row) pf2_store(Wb + BY * NP + x0, pf2_pack(p3, p4));
-        if (extra_row && extra_col) Wb[BY * NP + n] = p5;
+        pf2_store(Wb + w * NP + x0, pf2_pack(wv(p0, q0), wv(p1, q1)));
+        if (extra_col) Wb[w * NP + n] = wv(p2, q2);
+        if (extra_row) pf2_store(Wb + BY * NP + x0, pf2_pack(wv(p3, q3), wv(p4, q4)));
+        if (extra_row && extra_col) Wb[BY * NP + n] = wv(p5, q5);
     };
 
-    load_plane(z0, p0, p1, p2, p3, p4, p5);
+    load_plane(z0);
     store_plane(z0 % 3);
-    load_plane(z0 + 1, p0, p1, p2, p3, p4, p5);
+    load_plane(z0 + 1);
     store_plane((z0 + 1) % 3);
 
     if (t == 0) {  // node 0 has no element on its left: its shifted a = 1 slots stay 0
@@ -479,7 +484,7 @@ __global__ void __launch_bounds__(kV3Threads, MINB) stencil3d_v3_kernel(const St
     for (int k = z0; k < z1; ++k) {
         float* C = C2 + (k & 1) * 8 * BY * NP;
         const bool pf = (k + 2 <= z1);
-        if (pf) load_plane(k + 2, p0, p1, p2, p3, p4, p5);
+        if (pf) load_plane(k + 2);
         // operands of this layer's node epilogue (complete nodes of row yA only)
         const int idxA = k * sz32 + yA * sy32 + x0;
         const bool rowComplete = !(k == 0 || bndA || faceA || k == z0);
@@ -808,10 +813,10 @@ static jfnk_status launch_v3_pmb(const StencilArgs<float>& a, cudaStream_t st) {
     return JFNK_OK;
 }
 
-// a.v3 = 1: one CTA per SM (up to 128 registers a thread); 2: two CTAs per SM
-// (64 registers; the Chebyshev modes spill 50-160 bytes a thread to local
-// memory); otherwise two for the residual, FD-action and b - Jv modes and one
-// for the Chebyshev modes, the faster choice for each on 129^3-257^3 grids.
+// a.v3 = 1: one CTA per SM (up to 128 registers a thread; the default, the
+// faster choice in every mode on 129^3-257^3 grids); 2: two CTAs per SM (64
+// registers; 100-190 bytes a thread spill to local memory); otherwise two for
+// the residual, FD-action and b - Jv modes and one for the Chebyshev modes.
 template <Prob P, Mode M>
 static jfnk_status launch_v3_pm(const StencilArgs<float>& a, cudaStream_t st) {
     constexpr bool cheb = M == Mode::CHEB0 || M == Mode::CHEB || M == Mode::CHEBLAST;

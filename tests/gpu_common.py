@@ -47,9 +47,11 @@ KERNEL_PATHS = {
     "tiled": {"JFNK_EP3D_MAX_N_F64": "0", "JFNK_EP3D_MAX_N_F32": "0"},
     "v2": {"JFNK_EP3D_MAX_N_F64": "0", "JFNK_EP3D_MAX_N_F32": "0", "JFNK_V3_F32": "0"},
     # the two-elements-per-thread kernel with one / two CTAs per SM in every
-    # mode (by default the Chebyshev modes take one and the others two)
+    # mode (one is the default)
     "v3one": {"JFNK_EP3D_MAX_N_F64": "0", "JFNK_EP3D_MAX_N_F32": "0", "JFNK_V3_F32": "1"},
     "v3two": {"JFNK_EP3D_MAX_N_F64": "0", "JFNK_EP3D_MAX_N_F32": "0", "JFNK_V3_F32": "2"},
+    # two CTAs per SM for the residual, FD-action and b - Jv modes, one for the Chebyshev modes
+    "v3mixed": {"JFNK_EP3D_MAX_N_F64": "0", "JFNK_EP3D_MAX_N_F32": "0", "JFNK_V3_F32": "3"},
 }
 
 

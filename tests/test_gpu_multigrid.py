@@ -142,7 +142,8 @@ def test_chebyshev_smoother_parity(kind, n, levels, path, nu, zero, monkeypatch)
     assert rel(host(s), so) <= _fd_tol(so, se)
 
 
-@pytest.mark.parametrize("n,levels,path", [(64, 5, p) for p in ("default", "tiled", "v2", "v3two", "ep", "zm")]
+@pytest.mark.parametrize("n,levels,path", [(64, 5, p) for p in ("default", "tiled", "v2", "v3two", "v3mixed", "ep",
+                                                                  "zm")]
                          + [(32, 4, p) for p in ("default", "ep", "zm", "cluster")])
 def test_chebyshev_smoother_fp32_3d(n, levels, path, monkeypatch):
     """FP32 smoothing on the finest level of a 65^3 / 33^3 hierarchy (on the
