@@ -166,8 +166,8 @@ void jfnk_paper_options(jfnk_options* opts);
  *   JFNK_V2_THREADS_F64 / _F32  CTA-size cap of the halo-free kernel (default
  *                               1024; < 0: that kernel is not used)
  *   JFNK_V3_F32                 FP32 halo-free levels: 0 one element a thread,
- *                               1 (default) / 2 two elements a thread with one /
- *                               two CTAs per SM, 3 two, CTAs chosen per mode
+ *                               1 / 2 two elements a thread with one / two CTAs
+ *                               per SM, 3 (default) two, CTAs chosen per mode
  *   JFNK_ZM3D_MIN_N_F64 / _F32  element-parallel levels with n >= this (> 0)
  *                               march element columns along z (default 0: no)
  *   JFNK_EP3D_CLUSTER_MIN_N / _MAX_N  FP32 element-parallel levels with n in

@@ -147,7 +147,7 @@ struct jfnk_problem {
     int v2_threads32 = 1024;
     // FP32 levels on the halo-free tiling run its paired-element variant
     // (0: not used; 1 / 2: one / two CTAs per SM; 3: chosen per mode)
-    int v3_f32 = 1;
+    int v3_f32 = 3;
     // captured V-cycle (Lf.b -> Lf.s) and the options it was captured for
     cudaGraphExec_t vgraph = nullptr;
     cudaStream_t cap_stream = nullptr;

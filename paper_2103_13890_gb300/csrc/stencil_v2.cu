@@ -813,14 +813,14 @@ static jfnk_status launch_v3_pmb(const StencilArgs<float>& a, cudaStream_t st) {
     return JFNK_OK;
 }
 
-// a.v3 = 1: one CTA per SM (up to 128 registers a thread; the default, the
-// faster choice in every mode on 129^3-257^3 grids); 2: two CTAs per SM (64
-// registers; 100-190 bytes a thread spill to local memory); otherwise two for
-// the residual, FD-action and b - Jv modes and one for the Chebyshev modes.
+// a.v3 = 1: one CTA per SM (up to 128 registers a thread); 2: two CTAs per SM
+// (64 registers; the modes that read a direction spill 100-190 bytes a thread
+// to local memory); otherwise (the default) two for the residual, whose loads
+// are half as many and which spills 16-28 bytes, and one for the other modes:
+// the faster choice for each on 129^3-257^3 grids.
 template <Prob P, Mode M>
 static jfnk_status launch_v3_pm(const StencilArgs<float>& a, cudaStream_t st) {
-    constexpr bool cheb = M == Mode::CHEB0 || M == Mode::CHEB || M == Mode::CHEBLAST;
-    const bool two = a.v3 == 2 || (a.v3 != 1 && !cheb);
+    const bool two = a.v3 == 2 || (a.v3 != 1 && M == Mode::F);
     return two ? launch_v3_pmb<P, M, 2>(a, st) : launch_v3_pmb<P, M, 1>(a, st);
 }
 

@@ -47,10 +47,10 @@ KERNEL_PATHS = {
     "tiled": {"JFNK_EP3D_MAX_N_F64": "0", "JFNK_EP3D_MAX_N_F32": "0"},
     "v2": {"JFNK_EP3D_MAX_N_F64": "0", "JFNK_EP3D_MAX_N_F32": "0", "JFNK_V3_F32": "0"},
     # the two-elements-per-thread kernel with one / two CTAs per SM in every
-    # mode (one is the default)
+    # mode (by default the residual takes two and the other modes one)
     "v3one": {"JFNK_EP3D_MAX_N_F64": "0", "JFNK_EP3D_MAX_N_F32": "0", "JFNK_V3_F32": "1"},
     "v3two": {"JFNK_EP3D_MAX_N_F64": "0", "JFNK_EP3D_MAX_N_F32": "0", "JFNK_V3_F32": "2"},
-    # two CTAs per SM for the residual, FD-action and b - Jv modes, one for the Chebyshev modes
+    # the per-mode choice of the default
     "v3mixed": {"JFNK_EP3D_MAX_N_F64": "0", "JFNK_EP3D_MAX_N_F32": "0", "JFNK_V3_F32": "3"},
 }
 

@@ -47,9 +47,10 @@ CASES = [("bratu2d", 7), ("bratu2d", 64), ("bratu2d", 95), ("bratu2d", 600),
 PATH_CASES = [(k, n, path) for k, n in CASES for path in ("default", "ep", "zm", "tiled")
               if k != "bratu2d" or path == "default"]
 # the FP32 one-element-per-thread halo-free kernel (the default FP32 kernel on
-# these grids evaluates two elements per thread, one CTA per SM), the paired
-# kernel with two CTAs per SM or a per-mode choice, and the 129^3 grid in FP32
-PATH_CASES += [(k, n, path) for k, n in CASES for path in ("v2", "v3two", "v3mixed")
+# these grids evaluates two elements per thread, CTAs per SM chosen per mode),
+# the paired kernel with one or two CTAs per SM in every mode, and the 129^3
+# grid in FP32
+PATH_CASES += [(k, n, path) for k, n in CASES for path in ("v2", "v3one", "v3two")
                if k != "bratu2d" and n % 32 == 0 and n >= 64]
 PATH_CASES += [("nd3d", 128, "default")]
 # FP32 levels in one thread-block cluster: whole slices a CTA (n = 4, 16), two
